@@ -1,0 +1,369 @@
+/*
+ * oracle/binar_oracle.c -- CPU oracle for binar sort.  TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg may load
+ * this library.  It shares no code, header or table with the CUDA library: it is
+ * a plain, slow, obviously correct restatement of what the method computes.
+ *
+ * Contents (each function cites the passage it follows):
+ *   oracle_map_keys          the order-preserving bit string of a key ("The Other
+ *                            Universal Property": two's complement, IEEE-754, byte
+ *                            strings are sorted by their encoding)
+ *   oracle_binar_sort        the paper's in-place binar sort ("Operation of
+ *                            Algorithm", four steps; "Illustration of the
+ *                            Algorithm"), recursive, unstable
+ *   oracle_binar_sort_parallel  the paper's parallel variant ("Algorithm
+ *                            Variants": processor p sorts the elements whose
+ *                            leading bits spell p), used only for CPU timing
+ *   oracle_stable_radix      stable binary radix sort (LSD, one bit per pass):
+ *                            the definition-level oracle for record order when
+ *                            equal keys must keep their input order ("Sorting
+ *                            Formalism": the permutation p with K_p(1) <= ... )
+ *   oracle_partition_pass    one stable split of a range into 2^k sub-arrays by
+ *                            k bits at bit position pos (the partition step,
+ *                            generalised to k bits as in the parallel variant)
+ *
+ * Key layout: n keys of kb bytes each, as raw bytes.  Integer and float keys are
+ * little-endian machine words (kb = 1, 2, 4, 8, 16 for integers; 4, 8 for
+ * floats).  BYTES_BE keys are byte strings compared as big-endian bit strings
+ * (byte 0 most significant).  Payloads ("records", Sorting Formalism) are vb
+ * opaque bytes per key and move with their key.
+ *
+ * Bit numbering follows the paper's listing: position 0 is the most significant
+ * bit of the encoding, and a sort over w bits looks at positions 0 .. w-1 (the
+ * worked example uses w = 4 on nybbles stored in the high half of a byte).
+ *
+ * Parity pins for every function live in tests/test_oracle_*.py.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+enum { MAP_UNSIGNED = 0, MAP_SIGNED = 1, MAP_FLOAT = 2, MAP_BYTES_BE = 3 };
+
+/* --------------------------------------------------------------------------
+ * Encoding ("The Other Universal Property").
+ *
+ * key_bit returns bit `pos` (0 = most significant) of the order-preserving
+ * encoding of one key, written from the definitions of the encodings:
+ *  - unsigned: the binary numeral itself; the most significant byte of a
+ *    little-endian word is its last byte.
+ *  - signed (two's complement): the sign bit has weight -2^(w-1); inverting it
+ *    turns the order of signed values into the order of unsigned numerals.
+ *  - float (IEEE-754 sign-magnitude): a positive value orders by its magnitude
+ *    bits once the sign bit is set to 1; a negative value orders in reverse of
+ *    its magnitude, so every bit is inverted (its sign bit becomes 0).
+ *  - byte strings: lexicographic byte order is the order of the big-endian
+ *    bit string.
+ * ------------------------------------------------------------------------ */
+static int key_bit(const uint8_t *key, int kb, int map, int pos)
+{
+    if (map == MAP_BYTES_BE)
+        return (key[pos / 8] >> (7 - pos % 8)) & 1;
+
+    const uint8_t msb_byte = key[kb - 1];
+    int b = (key[kb - 1 - pos / 8] >> (7 - pos % 8)) & 1;
+    if (map == MAP_SIGNED) {
+        if (pos == 0) b = !b;
+    } else if (map == MAP_FLOAT) {
+        int negative = msb_byte >> 7;
+        if (negative) b = !b;
+        else if (pos == 0) b = !b;
+    }
+    return b;
+}
+
+/* Writes the encoding of each key as a big-endian byte string of kb bytes.
+ * Returns 0, or -1 for an unsupported (kb, map). */
+int oracle_map_keys(const uint8_t *keys, uint8_t *mapped, int64_t n, int kb, int map)
+{
+    if (kb <= 0 || kb > 16) return -1;
+    if (map == MAP_FLOAT && kb != 4 && kb != 8) return -1;
+    if (map < 0 || map > 3) return -1;
+    for (int64_t i = 0; i < n; i++) {
+        const uint8_t *k = keys + i * kb;
+        uint8_t *m = mapped + i * kb;
+        memset(m, 0, (size_t)kb);
+        for (int pos = 0; pos < 8 * kb; pos++)
+            if (key_bit(k, kb, map, pos)) m[pos / 8] |= (uint8_t)(0x80 >> (pos % 8));
+    }
+    return 0;
+}
+
+/* --------------------------------------------------------------------------
+ * Records.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    uint8_t *keys;
+    uint8_t *vals;      /* may be NULL */
+    int kb, vb, map, w;
+    int64_t visits;     /* element placements done by the partition step */
+    /* optional trace of every partition configuration (worked example) */
+    int64_t *trace;
+    int64_t trace_cap, trace_len;
+    int64_t n;
+} records;
+
+static void exchange(records *r, int64_t i, int64_t j)
+{
+    uint8_t t[16];
+    if (i == j) return;
+    memcpy(t, r->keys + i * r->kb, (size_t)r->kb);
+    memcpy(r->keys + i * r->kb, r->keys + j * r->kb, (size_t)r->kb);
+    memcpy(r->keys + j * r->kb, t, (size_t)r->kb);
+    if (r->vals && r->vb > 0) {
+        uint8_t u[16];
+        memcpy(u, r->vals + i * r->vb, (size_t)r->vb);
+        memcpy(r->vals + i * r->vb, r->vals + j * r->vb, (size_t)r->vb);
+        memcpy(r->vals + j * r->vb, u, (size_t)r->vb);
+    }
+}
+
+static int bit_of(const records *r, int64_t i, int pos)
+{
+    return key_bit(r->keys + i * r->kb, r->kb, r->map, pos);
+}
+
+/* One trace row: pos, lower, upper, lo, hi, then the first key byte of every
+ * element (the worked example sorts 1-byte keys). */
+static void trace_state(records *r, int pos, int64_t lower, int64_t upper,
+                        int64_t lo, int64_t hi)
+{
+    if (!r->trace) return;
+    int64_t row = 5 + r->n;
+    if (r->trace_len + row > r->trace_cap) return;
+    int64_t *t = r->trace + r->trace_len;
+    t[0] = pos; t[1] = lower; t[2] = upper; t[3] = lo; t[4] = hi;
+    for (int64_t i = 0; i < r->n; i++) t[5 + i] = r->keys[i * r->kb];
+    r->trace_len += row;
+}
+
+/* --------------------------------------------------------------------------
+ * Binar sort ("Operation of Algorithm").  The four steps, in the paper's order:
+ *   1. base case: stop when the bit positions are used up or the sub-array
+ *      holds at most one element;
+ *   2. initialise the working bounds lo/hi from the passed bounds lower/upper;
+ *   3. partition: extract bit `pos` of the element at the lower working bound;
+ *      a zero leaves it in the lower sub-array (lo moves up), a one exchanges it
+ *      with the element at the upper working bound (hi moves down); repeat until
+ *      the bounds cross;
+ *   4. recursive call: if one of the two sub-arrays is empty the array passed
+ *      through undivided and is partitioned again on the next bit; otherwise
+ *      the lower sub-array [lower, lo-1] and the upper one [lo, upper] are each
+ *      partitioned on the next bit.
+ * Indices are signed 64-bit so that hi may step below lower without wrapping.
+ * ------------------------------------------------------------------------ */
+static void binar(records *r, int64_t lower, int64_t upper, int pos)
+{
+    /* step 1 */
+    if (pos >= r->w || upper - lower + 1 <= 1) return;
+
+    /* step 2 */
+    int64_t lo = lower, hi = upper;
+    trace_state(r, pos, lower, upper, lo, hi);
+
+    /* step 3 */
+    while (lo <= hi) {
+        r->visits++;
+        if (bit_of(r, lo, pos) == 0) {
+            lo = lo + 1;
+        } else {
+            exchange(r, lo, hi);
+            hi = hi - 1;
+        }
+        trace_state(r, pos, lower, upper, lo, hi);
+    }
+
+    /* step 4 */
+    int lower_empty = (lo == lower);
+    int upper_empty = (lo == upper + 1);
+    if (lower_empty || upper_empty) {
+        binar(r, lower, upper, pos + 1);            /* pass-through */
+    } else {
+        binar(r, lower, lo - 1, pos + 1);
+        binar(r, lo, upper, pos + 1);
+    }
+}
+
+static int check_args(int64_t n, int kb, int map, int vb, int w)
+{
+    if (n < 0 || kb <= 0 || kb > 16 || vb < 0 || vb > 16) return -1;
+    if (map < 0 || map > 3) return -1;
+    if (map == MAP_FLOAT && kb != 4 && kb != 8) return -1;
+    if (w < 0 || w > 8 * kb) return -1;
+    return 0;
+}
+
+/* Sorts each segment [offsets[s], offsets[s+1]) in place with binar sort on
+ * bit positions 0 .. w-1.  Returns the number of element placements (the
+ * quantity the time analysis bounds by w per element), or -1 on bad arguments. */
+int64_t oracle_binar_sort(uint8_t *keys, uint8_t *vals, const int64_t *offsets,
+                          int64_t num_segments, int kb, int map, int vb, int w)
+{
+    if (check_args(0, kb, map, vb, w) || num_segments < 0) return -1;
+    records r = {keys, vals, kb, vb, map, w, 0, NULL, 0, 0, 0};
+    for (int64_t s = 0; s < num_segments; s++) {
+        if (offsets[s + 1] < offsets[s]) return -1;
+        binar(&r, offsets[s], offsets[s + 1] - 1, 0);
+    }
+    return r.visits;
+}
+
+/* Binar sort of one array with every partition configuration recorded (rows
+ * of 5 + n int64: pos, lower, upper, lo, hi, key bytes).  Returns the number of
+ * int64 written, or -1. */
+int64_t oracle_binar_sort_trace(uint8_t *keys, int64_t n, int kb, int map, int w,
+                                int64_t *trace, int64_t trace_cap)
+{
+    if (check_args(n, kb, map, 0, w)) return -1;
+    records r = {keys, NULL, kb, 0, map, w, 0, trace, trace_cap, 0, n};
+    binar(&r, 0, n - 1, 0);
+    return r.trace_len;
+}
+
+/* --------------------------------------------------------------------------
+ * Parallel variant ("Algorithm Variants"): one counting pass groups the
+ * elements by their leading b bits (processor p gets the elements whose leading
+ * bits spell p); then every group is binar-sorted from bit b on, independently,
+ * one thread per group.  Used only to time the oracle on all host cores.
+ * ------------------------------------------------------------------------ */
+typedef struct { records r; int64_t lower, upper; int pos; } group_job;
+
+static void *group_worker(void *arg)
+{
+    group_job *g = (group_job *)arg;
+    binar(&g->r, g->lower, g->upper, g->pos);
+    return NULL;
+}
+
+int64_t oracle_binar_sort_parallel(uint8_t *keys, uint8_t *vals, int64_t n, int kb,
+                                   int map, int vb, int w, int log2_groups)
+{
+    if (check_args(n, kb, map, vb, w) || log2_groups < 0 || log2_groups > 12) return -1;
+    int b = log2_groups < w ? log2_groups : w;
+    int64_t groups = (int64_t)1 << b;
+    int64_t *count = calloc((size_t)groups + 1, sizeof(int64_t));
+    uint8_t *tk = malloc((size_t)(n * kb + 1));
+    uint8_t *tv = (vals && vb) ? malloc((size_t)(n * vb + 1)) : NULL;
+    int64_t *gid = malloc((size_t)(n + 1) * sizeof(int64_t));
+    group_job *jobs = calloc((size_t)groups, sizeof(group_job));
+    pthread_t *th = calloc((size_t)groups, sizeof(pthread_t));
+    if (!count || !tk || !gid || !jobs || !th || (vals && vb && !tv)) return -1;
+
+    for (int64_t i = 0; i < n; i++) {
+        int64_t g = 0;
+        for (int p = 0; p < b; p++) g = 2 * g + key_bit(keys + i * kb, kb, map, p);
+        gid[i] = g;
+        count[g + 1]++;
+    }
+    for (int64_t g = 0; g < groups; g++) count[g + 1] += count[g];
+    int64_t *next = calloc((size_t)groups, sizeof(int64_t));
+    for (int64_t g = 0; g < groups; g++) next[g] = count[g];
+    for (int64_t i = 0; i < n; i++) {
+        int64_t d = next[gid[i]]++;
+        memcpy(tk + d * kb, keys + i * kb, (size_t)kb);
+        if (tv) memcpy(tv + d * vb, vals + i * vb, (size_t)vb);
+    }
+    memcpy(keys, tk, (size_t)(n * kb));
+    if (tv) memcpy(vals, tv, (size_t)(n * vb));
+
+    int64_t visits = n; /* the counting pass looks at every element once */
+    for (int64_t g = 0; g < groups; g++) {
+        records r = {keys, vals, kb, vb, map, w, 0, NULL, 0, 0, 0};
+        jobs[g].r = r;
+        jobs[g].lower = count[g];
+        jobs[g].upper = count[g + 1] - 1;
+        jobs[g].pos = b;
+        pthread_create(&th[g], NULL, group_worker, &jobs[g]);
+    }
+    for (int64_t g = 0; g < groups; g++) {
+        pthread_join(th[g], NULL);
+        visits += jobs[g].r.visits;
+    }
+    free(count); free(next); free(tk); free(tv); free(gid); free(jobs); free(th);
+    return visits;
+}
+
+/* --------------------------------------------------------------------------
+ * Stable binary radix sort ("Sorting Formalism": among the permutations that
+ * order the keys, the stable one keeps equal keys in their input order).
+ * Least significant bit first, one bit per pass, each pass a stable split of
+ * the segment into the elements whose bit is 0 followed by those whose bit is 1.
+ * After the pass on bit 0 (the most significant) the segment is ordered by all
+ * w bits, and equal keys are in input order because every pass kept it.
+ * ------------------------------------------------------------------------ */
+int oracle_stable_radix(uint8_t *keys, uint8_t *vals, const int64_t *offsets,
+                        int64_t num_segments, int kb, int map, int vb, int w)
+{
+    if (check_args(0, kb, map, vb, w) || num_segments < 0) return -1;
+    int64_t maxlen = 0;
+    for (int64_t s = 0; s < num_segments; s++) {
+        if (offsets[s + 1] < offsets[s]) return -1;
+        if (offsets[s + 1] - offsets[s] > maxlen) maxlen = offsets[s + 1] - offsets[s];
+    }
+    uint8_t *tk = malloc((size_t)(maxlen * kb + 1));
+    uint8_t *tv = malloc((size_t)(maxlen * (vb > 0 ? vb : 1) + 1));
+    if (!tk || !tv) return -1;
+    for (int64_t s = 0; s < num_segments; s++) {
+        int64_t first = offsets[s], len = offsets[s + 1] - offsets[s];
+        uint8_t *k = keys + first * kb;
+        uint8_t *v = (vals && vb) ? vals + first * vb : NULL;
+        for (int pos = w - 1; pos >= 0; pos--) {
+            int64_t zeros = 0;
+            for (int64_t i = 0; i < len; i++)
+                if (key_bit(k + i * kb, kb, map, pos) == 0) zeros++;
+            int64_t at0 = 0, at1 = zeros;
+            for (int64_t i = 0; i < len; i++) {
+                int64_t d = key_bit(k + i * kb, kb, map, pos) ? at1++ : at0++;
+                memcpy(tk + d * kb, k + i * kb, (size_t)kb);
+                if (v) memcpy(tv + d * vb, v + i * vb, (size_t)vb);
+            }
+            memcpy(k, tk, (size_t)(len * kb));
+            if (v) memcpy(v, tv, (size_t)(len * vb));
+        }
+    }
+    free(tk); free(tv);
+    return 0;
+}
+
+/* --------------------------------------------------------------------------
+ * One partition pass, k bits at a time: the records of [0, n) are split,
+ * stably, into 2^k sub-arrays by the digit formed by bits pos .. pos+k-1 of
+ * the encoding (bits past the end of the key read as 0).  Sub-array d is
+ * written to [offsets[d], offsets[d+1]) of the output.  With k = 1 this is the
+ * paper's lower/upper split with the input order kept inside each sub-array.
+ * ------------------------------------------------------------------------ */
+int oracle_partition_pass(const uint8_t *keys_in, const uint8_t *vals_in,
+                          uint8_t *keys_out, uint8_t *vals_out, int64_t n,
+                          int kb, int map, int vb, int pos, int k, int64_t *offsets)
+{
+    if (check_args(n, kb, map, vb, 8 * kb) || k < 1 || k > 16 || pos < 0 || pos >= 8 * kb)
+        return -1;
+    int64_t radix = (int64_t)1 << k;
+    int64_t *digit = malloc((size_t)(n + 1) * sizeof(int64_t));
+    if (!digit) return -1;
+    for (int64_t d = 0; d <= radix; d++) offsets[d] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t d = 0;
+        for (int j = 0; j < k; j++) {
+            int p = pos + j;
+            int b = p < 8 * kb ? key_bit(keys_in + i * kb, kb, map, p) : 0;
+            d = 2 * d + b;
+        }
+        digit[i] = d;
+        offsets[d + 1]++;
+    }
+    for (int64_t d = 0; d < radix; d++) offsets[d + 1] += offsets[d];
+    int64_t *next = malloc((size_t)radix * sizeof(int64_t));
+    if (!next) { free(digit); return -1; }
+    for (int64_t d = 0; d < radix; d++) next[d] = offsets[d];
+    for (int64_t i = 0; i < n; i++) {
+        int64_t at = next[digit[i]]++;
+        memcpy(keys_out + at * kb, keys_in + i * kb, (size_t)kb);
+        if (vals_in && vals_out && vb)
+            memcpy(vals_out + at * vb, vals_in + i * vb, (size_t)vb);
+    }
+    free(digit); free(next);
+    return 0;
+}
