@@ -20,6 +20,9 @@ function computes, and the passage of the paper it restates:
 * :func:`stable_radix` -- stable binary LSD radix sort, the record-order oracle
   ("Sorting Formalism" with equal keys kept in input order).
 * :func:`partition_pass` -- one stable k-bit partition at bit position ``pos``.
+* :func:`rank_of` / :func:`occurrence` -- the output position range of one key
+  and the input index of its j-th copy, by definition, for checking sampled
+  outputs of sorts too large for the other functions.
 
 Parity pins: ``tests/test_oracle_*.py`` (no GPU needed).
 """
@@ -68,6 +71,10 @@ def configure(lib):
     lib.oracle_stable_radix.restype = i32
     lib.oracle_partition_pass.argtypes = [p, p, p, p, i64, i32, i32, i32, i32, i32, p]
     lib.oracle_partition_pass.restype = i32
+    lib.oracle_rank_of.argtypes = [p, i64, i32, i32, p, p, p]
+    lib.oracle_rank_of.restype = i32
+    lib.oracle_occurrence.argtypes = [p, i64, i32, p, i64]
+    lib.oracle_occurrence.restype = i64
     return lib
 
 
@@ -187,3 +194,23 @@ def partition_pass(keys, vals=None, key_map=MAP_UNSIGNED, pos=0, k=8):
                                      key_map, vb, pos, k, _ptr(offs)) != 0:
         raise ValueError("oracle_partition_pass: bad arguments")
     return ko, vo, offs
+
+
+def rank_of(keys, probe, key_map=MAP_UNSIGNED):
+    """(number of keys below probe, number not above probe) by the encoding."""
+    kv, kb = _key_view(keys)
+    pr = np.ascontiguousarray(np.asarray(probe)).view(np.uint8).reshape(-1)
+    if pr.shape[0] != kb:
+        raise ValueError("probe must be one key")
+    lt, le = ctypes.c_int64(0), ctypes.c_int64(0)
+    if _load().oracle_rank_of(_ptr(kv), kv.shape[0], kb, key_map, _ptr(pr), ctypes.byref(lt),
+                              ctypes.byref(le)) != 0:
+        raise ValueError("oracle_rank_of: bad arguments")
+    return lt.value, le.value
+
+
+def occurrence(keys, probe, j):
+    """Input index of the j-th (0-based) key bit-identical to probe, or -1."""
+    kv, kb = _key_view(keys)
+    pr = np.ascontiguousarray(np.asarray(probe)).view(np.uint8).reshape(-1)
+    return int(_load().oracle_occurrence(_ptr(kv), kv.shape[0], kb, _ptr(pr), j))

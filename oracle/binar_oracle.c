@@ -367,3 +367,47 @@ int oracle_partition_pass(const uint8_t *keys_in, const uint8_t *vals_in,
     free(digit); free(next);
     return 0;
 }
+
+/* --------------------------------------------------------------------------
+ * Rank of one key by definition ("Sorting Formalism": in the sorted
+ * permutation a key K sits after every key smaller than K): counts the input
+ * keys whose encoding is below / not above that of `probe`.  With these, the
+ * key at any output position i of a sort can be checked on its own:
+ * less(K) <= i < less_or_equal(K).
+ * ------------------------------------------------------------------------ */
+static int compare_encoded(const uint8_t *a, const uint8_t *b, int kb, int map)
+{
+    for (int pos = 0; pos < 8 * kb; pos++) {
+        int x = key_bit(a, kb, map, pos), y = key_bit(b, kb, map, pos);
+        if (x != y) return x < y ? -1 : 1;
+    }
+    return 0;
+}
+
+int oracle_rank_of(const uint8_t *keys, int64_t n, int kb, int map, const uint8_t *probe,
+                   int64_t *less, int64_t *less_or_equal)
+{
+    if (check_args(n, kb, map, 0, 8 * kb)) return -1;
+    int64_t lt = 0, le = 0;
+    for (int64_t i = 0; i < n; i++) {
+        int c = compare_encoded(keys + i * kb, probe, kb, map);
+        if (c < 0) lt++;
+        if (c <= 0) le++;
+    }
+    *less = lt;
+    *less_or_equal = le;
+    return 0;
+}
+
+/* Index of the j-th (0-based) input key equal to `probe`, or -1: in the stable
+ * order the j-th copy of a key in the output is the j-th copy in the input. */
+int64_t oracle_occurrence(const uint8_t *keys, int64_t n, int kb, const uint8_t *probe, int64_t j)
+{
+    for (int64_t i = 0; i < n; i++) {
+        if (memcmp(keys + i * kb, probe, (size_t)kb) == 0) {
+            if (j == 0) return i;
+            j--;
+        }
+    }
+    return -1;
+}

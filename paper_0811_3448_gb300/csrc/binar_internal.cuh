@@ -1,0 +1,244 @@
+// binar_internal.cuh -- data structures shared by the host driver and the
+// kernels of libbinar: key encodings, bucket/job descriptors, the workspace
+// layout and small device helpers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/binar.h"
+
+namespace binar {
+
+// k: key bits consumed per partition pass.  The paper splits on one bit per
+// pass ("Partition Array into Sub-arrays"); fusing k = 8 bits does the work of
+// eight of its passes in one read and one write of every live key.
+constexpr int kBits = 8;
+constexpr int kRadix = 1 << kBits;
+constexpr int kThreads = 256;        // threads of every tile kernel (one per digit)
+constexpr int kWarps = kThreads / 32;
+
+// ---------------------------------------------------------------------------
+// Descriptors.  A Bucket is one live sub-array of the recursion: a contiguous
+// range of the key array that still has to be split on bits pos .. w-1.
+// ---------------------------------------------------------------------------
+enum BucketFlags : uint8_t {
+    kHasHist = 1,   // its digit histogram was computed by an earlier kernel
+    kSkip = 2,      // no partition at this level (pass-through or finished)
+};
+
+struct Bucket {
+    long long begin;       // first key index
+    uint32_t len;          // keys in the bucket (> the finisher cutoff)
+    uint32_t tile_start;   // first tile of the bucket in this level's tile space
+    uint16_t pos;          // next bit position to split on (0 = most significant)
+    uint8_t buf;           // 0: the caller's arrays, 1: the workspace arrays
+    uint8_t flags;         // BucketFlags
+    uint32_t pad;
+};
+static_assert(sizeof(Bucket) == 24, "Bucket layout");
+
+// A bucket small enough to finish inside one CTA's shared memory: it is sorted
+// on bits pos .. w-1 and written to the caller's arrays.
+struct Job {
+    long long begin;
+    uint32_t len;
+    uint16_t pos;          // == w: nothing left to sort, only move to buffer 0
+    uint8_t buf;
+    uint8_t pad;
+};
+static_assert(sizeof(Job) == 16, "Job layout");
+
+// A finished bucket larger than the finisher cutoff that sits in the
+// workspace arrays and must be copied back to the caller's arrays.
+struct CopyJob {
+    long long begin;
+    uint32_t len;
+    uint32_t tile_start;
+};
+static_assert(sizeof(CopyJob) == 16, "CopyJob layout");
+
+struct Counters {
+    uint32_t status;                  // first device error (binar_status), 0 = OK
+    uint32_t njobs;                   // finisher jobs
+    unsigned long long alloc[2];      // per list slot: (tiles << 32) | buckets
+    unsigned long long copy_alloc;    // (tiles << 32) | copy jobs
+    uint32_t ticket_hist, ticket_part, ticket_fin, ticket_copy;
+    uint32_t ticket_prep;
+    uint32_t pad[7];
+};
+static_assert(sizeof(Counters) == 80, "Counters layout");
+
+// Device view of the caller's workspace, carved by the host driver.
+struct Ws {
+    Counters *ctr;
+    void *alt_keys;                // n * key_bytes
+    void *alt_vals;                // n * val_bytes
+    Bucket *list[2];               // two list slots: current level / next level
+    uint32_t *hist[2];             // [bucket][kRadix]: counts, then exclusive prefix
+    uint4 *andor[2];               // [bucket][2]: AND and OR of the encoded keys
+    uint32_t *tilemap;             // [tile] -> bucket index in the current list
+    uint32_t *cells;               // [tile][kRadix] look-back cells
+    Job *jobs;
+    CopyJob *copies;
+    uint32_t mcap, tcap, jcap, ccap;   // capacities: buckets, tiles, jobs, copy jobs
+};
+
+// Per-call parameters shared by every kernel of one sort.
+struct Params {
+    void *keys;                    // caller's keys (buffer 0)
+    void *vals;                    // caller's payloads (buffer 0) or nullptr
+    long long n;
+    int map;                       // binar_key_map
+    int cutoff;                    // finisher cutoff C
+    long long timeout_ns;
+    int skip_publish_tile;         // test hook: level-0 tile that never publishes (-1 = none)
+};
+
+// ---------------------------------------------------------------------------
+// Key encodings ("The Other Universal Property"): every supported key type is
+// mapped to an unsigned bit string whose unsigned order is the key order.
+// Keys stay in their raw form in memory; the map is applied when a digit is
+// extracted.
+// ---------------------------------------------------------------------------
+struct U128 {
+    uint64_t hi, lo;
+};
+
+template <int KB> struct KeyTraits;
+
+template <> struct KeyTraits<4> {
+    using Raw = uint32_t;
+    using Bits = uint32_t;
+    static constexpr int kW = 32;
+    __device__ static __forceinline__ Bits encode(Raw x, int map) {
+        switch (map) {
+        case BINAR_MAP_SIGNED: return x ^ 0x80000000u;
+        case BINAR_MAP_FLOAT: return (x & 0x80000000u) ? ~x : (x | 0x80000000u);
+        case BINAR_MAP_BYTES_BE: return __byte_perm(x, 0, 0x0123);
+        default: return x;
+        }
+    }
+    __device__ static __forceinline__ uint32_t digit(Bits b, int pos) {
+        return (b << pos) >> (32 - kBits);       // pos < 32
+    }
+    __device__ static __forceinline__ Bits ones() { return 0xffffffffu; }
+    __device__ static __forceinline__ Bits zero() { return 0u; }
+    // first bit position (0 = MSB) where a and o differ, or kW if equal
+    __device__ static __forceinline__ int first_diff(Bits a, Bits o) {
+        return (a == o) ? kW : __clz(a ^ o);
+    }
+    __device__ static __forceinline__ uint4 pack(Bits b) { return make_uint4(b, 0, 0, 0); }
+    __device__ static __forceinline__ Bits unpack(uint4 v) { return v.x; }
+};
+
+template <> struct KeyTraits<8> {
+    using Raw = uint64_t;
+    using Bits = uint64_t;
+    static constexpr int kW = 64;
+    __device__ static __forceinline__ uint64_t bswap64(uint64_t x) {
+        uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+        return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
+    }
+    __device__ static __forceinline__ Bits encode(Raw x, int map) {
+        const uint64_t s = 0x8000000000000000ull;
+        switch (map) {
+        case BINAR_MAP_SIGNED: return x ^ s;
+        case BINAR_MAP_FLOAT: return (x & s) ? ~x : (x | s);
+        case BINAR_MAP_BYTES_BE: return bswap64(x);
+        default: return x;
+        }
+    }
+    __device__ static __forceinline__ uint32_t digit(Bits b, int pos) {
+        return (uint32_t)((b << pos) >> (64 - kBits));   // pos < 64
+    }
+    __device__ static __forceinline__ Bits ones() { return ~0ull; }
+    __device__ static __forceinline__ Bits zero() { return 0ull; }
+    __device__ static __forceinline__ int first_diff(Bits a, Bits o) {
+        return (a == o) ? kW : __clzll(a ^ o);
+    }
+    __device__ static __forceinline__ uint4 pack(Bits b) {
+        return make_uint4((uint32_t)b, (uint32_t)(b >> 32), 0, 0);
+    }
+    __device__ static __forceinline__ Bits unpack(uint4 v) { return ((uint64_t)v.y << 32) | v.x; }
+};
+
+template <> struct KeyTraits<16> {
+    using Raw = uint4;     // bytes 0..15 as four little-endian words x, y, z, w
+    using Bits = U128;
+    static constexpr int kW = 128;
+    __device__ static __forceinline__ Bits encode(Raw x, int map) {
+        Bits b;
+        if (map == BINAR_MAP_BYTES_BE) {
+            b.hi = ((uint64_t)__byte_perm(x.x, 0, 0x0123) << 32) | __byte_perm(x.y, 0, 0x0123);
+            b.lo = ((uint64_t)__byte_perm(x.z, 0, 0x0123) << 32) | __byte_perm(x.w, 0, 0x0123);
+        } else {   // little-endian 128-bit integer
+            b.hi = ((uint64_t)x.w << 32) | x.z;
+            b.lo = ((uint64_t)x.y << 32) | x.x;
+            if (map == BINAR_MAP_SIGNED) b.hi ^= 0x8000000000000000ull;
+        }
+        return b;
+    }
+    __device__ static __forceinline__ uint32_t digit(Bits b, int pos) {
+        uint64_t top;
+        if (pos < 64) top = pos ? ((b.hi << pos) | (b.lo >> (64 - pos))) : b.hi;
+        else top = b.lo << (pos - 64);
+        return (uint32_t)(top >> (64 - kBits));
+    }
+    __device__ static __forceinline__ Bits ones() { return Bits{~0ull, ~0ull}; }
+    __device__ static __forceinline__ Bits zero() { return Bits{0ull, 0ull}; }
+    __device__ static __forceinline__ int first_diff(Bits a, Bits o) {
+        uint64_t h = a.hi ^ o.hi, l = a.lo ^ o.lo;
+        if (h) return __clzll(h);
+        if (l) return 64 + __clzll(l);
+        return kW;
+    }
+    __device__ static __forceinline__ uint4 pack(Bits b) {
+        return make_uint4((uint32_t)b.lo, (uint32_t)(b.lo >> 32), (uint32_t)b.hi,
+                          (uint32_t)(b.hi >> 32));
+    }
+    __device__ static __forceinline__ Bits unpack(uint4 v) {
+        return Bits{((uint64_t)v.w << 32) | v.z, ((uint64_t)v.y << 32) | v.x};
+    }
+};
+
+__device__ __forceinline__ U128 operator&(U128 a, U128 b) { return U128{a.hi & b.hi, a.lo & b.lo}; }
+__device__ __forceinline__ U128 operator|(U128 a, U128 b) { return U128{a.hi | b.hi, a.lo | b.lo}; }
+
+template <int VB> struct ValTraits { using T = uint32_t; };
+template <> struct ValTraits<8> { using T = uint64_t; };
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void set_status(Counters *c, uint32_t code) {
+    atomicCAS(&c->status, 0u, code);
+}
+
+__device__ __forceinline__ bool has_error(const Counters *c) {
+    return ld_relaxed(&c->status) != 0;
+}
+
+}  // namespace binar

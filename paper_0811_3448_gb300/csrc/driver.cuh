@@ -1,0 +1,134 @@
+// driver.cuh -- host side of libbinar: workspace layout and the level loop
+// that runs the recursion of binar sort as a fixed sequence of kernel
+// launches ("Algorithm Variants": the recursion replaced by iteration, each
+// level handling every live sub-array at once).  Everything is enqueued on the
+// caller's stream; nothing allocates or synchronises.
+#pragma once
+
+#include "kernels.cuh"
+#include "layout.cuh"
+
+namespace binar {
+
+template <int KB, int VB, bool STABLE>
+int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int level,
+                     void *k0, void *k1, void *v0, void *v1) {
+    auto kfn = k_partition<KB, VB, STABLE>;
+    const size_t smem = sizeof(PartitionSmem<KB, VB, STABLE>);
+    int occ = kernel_ctas_per_sm((const void *)kfn, smem);
+    if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
+    const int grid = device_sms() * (occ > 0 ? occ : 1);
+    return launch("partition", level, c.stream, [&] {
+        kfn<<<grid, kThreads, smem, c.stream>>>(ws, p, slot, level, k0, k1, v0, v1);
+    });
+}
+
+template <int KB, int VB>
+int run_call_vb(const Call &c) {
+    constexpr int T = TileShape<KB>::kTile;
+    constexpr int STABLE = VB > 0;
+    const int L = levels_for(KB);
+    const int sms = device_sms();
+    if (sms <= 0) return BINAR_ERR_CUDA;
+    const Layout lay = make_layout(c.n, c.offsets ? c.num_segments : 1, KB, VB);
+    const Ws ws = carve(lay, c.ws);
+    Params p{};
+    p.map = c.map;
+    p.n = c.n;
+    p.cutoff = c.cutoff;
+    p.timeout_ns = c.timeout_ns;
+    p.skip_publish_tile = c.skip_publish_tile;
+    const int small_grid = sms * 4;
+    int rc;
+
+    if (c.pass_mode) {
+        p.keys = const_cast<void *>(c.keys_in);
+        p.vals = const_cast<void *>(c.vals_in);
+        const uint32_t tiles = (uint32_t)((c.n + T - 1) / T);
+        if ((rc = launch("init", -1, c.stream, [&] {
+                 k_init<<<1, 1, 0, c.stream>>>(ws, c.n, 0, c.pass_pos, tiles, 1);
+             })))
+            return rc;
+        if ((rc = launch("prep", 0, c.stream, [&] { k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, 0); })))
+            return rc;
+        {
+            auto hfn = k_hist<KB>;
+            const int occ = kernel_ctas_per_sm((const void *)hfn, 0);
+            if ((rc = launch("hist", 0, c.stream, [&] {
+                     hfn<<<sms * (occ > 0 ? occ : 1), kThreads, 0, c.stream>>>(ws, p, 0, 0);
+                 })))
+                return rc;
+        }
+        if ((rc = launch("prefix", -1, c.stream, [&] {
+                 k_prefix_only<<<1, kThreads, 0, c.stream>>>(ws, c.pass_offsets, c.n);
+             })))
+            return rc;
+        return launch_partition<KB, VB, true>(c, ws, p, 0, 1, const_cast<void *>(c.keys_in),
+                                              c.keys_out, const_cast<void *>(c.vals_in), c.vals_out);
+    }
+
+    p.keys = c.keys;
+    p.vals = c.vals;
+    void *k0 = c.keys, *k1 = ws.alt_keys, *v0 = c.vals, *v1 = VB ? ws.alt_vals : nullptr;
+    const bool seg = c.offsets != nullptr;
+    const uint32_t tiles0 = (uint32_t)((c.n + T - 1) / T);
+    if ((rc = launch("init", -1, c.stream, [&] {
+             k_init<<<1, 1, 0, c.stream>>>(ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
+         })))
+        return rc;
+    if (seg) {
+        const long long S = c.num_segments;
+        int grid = (int)((S + kThreads - 1) / kThreads);
+        if (grid > small_grid) grid = small_grid;
+        if (grid < 1) grid = 1;
+        if ((rc = launch("seed", -1, c.stream, [&] {
+                 k_seed_segments<<<grid, kThreads, 0, c.stream>>>(ws, c.offsets, S, c.n, c.cutoff, T);
+             })))
+            return rc;
+    }
+    if (seg || c.n > c.cutoff) {
+        auto hfn = k_hist<KB>;
+        const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
+        const int hgrid = sms * (hocc > 0 ? hocc : 1);
+        for (int l = 0; l < L; l++) {
+            const int slot = l & 1;
+            if ((rc = launch("prep", l, c.stream, [&] {
+                     k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, slot);
+                 })))
+                return rc;
+            if ((rc = launch("hist", l, c.stream, [&] {
+                     hfn<<<hgrid, kThreads, 0, c.stream>>>(ws, p, slot, 0);
+                 })))
+                return rc;
+            if ((rc = launch("classify", l, c.stream, [&] {
+                     k_classify<KB><<<small_grid, kThreads, 0, c.stream>>>(ws, p, slot, l == L - 1);
+                 })))
+                return rc;
+            if ((rc = launch_partition<KB, VB, STABLE>(c, ws, p, slot, l, k0, k1, v0, v1))) return rc;
+        }
+    }
+    {
+        auto ffn = k_finish<KB, VB>;
+        const size_t smem = sizeof(FinishSmem<KB, VB>);
+        const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
+        if ((rc = launch("finish", -1, c.stream, [&] {
+                 ffn<<<sms * (occ > 0 ? occ : 1), kThreads, smem, c.stream>>>(ws, p, k0, k1, v0, v1);
+             })))
+            return rc;
+    }
+    return launch("copy", -1, c.stream, [&] {
+        k_copy<KB, VB><<<small_grid, kThreads, 0, c.stream>>>(ws, k0, k1, v0, v1);
+    });
+}
+
+template <int KB>
+int run_call(const Call &c) {
+    switch (c.vb) {
+    case 0: return run_call_vb<KB, 0>(c);
+    case 4: return run_call_vb<KB, 4>(c);
+    case 8: return run_call_vb<KB, 8>(c);
+    default: return BINAR_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace binar

@@ -1,0 +1,936 @@
+// kernels.cuh -- the CUDA kernels of libbinar (sm_103a).
+//
+// The paper's binar sort ("Operation of Algorithm") splits a sub-array on one
+// bit, then recurses into the two parts.  Here every level of that recursion
+// is run for all live sub-arrays ("buckets") at once and k = 8 bits at a time:
+//
+//   prep      builds the level's tile -> bucket map, clears its look-back cells
+//             and histograms                         (bookkeeping of step 2)
+//   hist      per bucket: digit counts at its bit position, and the AND / OR
+//             of its encoded keys                     (bit extraction, step 3)
+//   classify  per bucket: base case, pass-through or split; children become
+//             next-level buckets, finisher jobs or copy jobs   (steps 1 and 4)
+//   partition per tile: stable rank by digit, single-pass decoupled look-back
+//             across the bucket's tiles, scatter through shared memory (step 3)
+//   finish    per small bucket: the rest of the recursion in shared memory
+//   copy      moves finished buckets that sit in the workspace back
+#pragma once
+
+#include "binar_internal.cuh"
+
+namespace binar {
+
+// Items per thread of a tile, by key size: 8192 / 4096 / 2048 keys per tile.
+template <int KB> struct TileShape {
+    static constexpr int kItems = KB == 4 ? 32 : (KB == 8 ? 16 : 8);
+    static constexpr int kTile = kThreads * kItems;
+};
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one uint32 per thread (kThreads threads).
+// `scratch` holds kWarps words.  Returns the exclusive prefix; *total gets the
+// sum.  Contains two __syncthreads().
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *scratch,
+                                                         uint32_t *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) scratch[w] = incl;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+#pragma unroll
+    for (int i = 0; i < kWarps; i++) {
+        uint32_t s = scratch[i];
+        before += (i < w) ? s : 0u;
+        all += s;
+    }
+    __syncthreads();
+    *total = all;
+    return before + incl - v;
+}
+
+// ---------------------------------------------------------------------------
+// Tile ranking.  A tile of up to kThreads * ITEMS keys is held "warp-striped":
+// item j of lane l in warp w is tile element w*32*ITEMS + j*32 + l, so the
+// processing order (warp, item, lane) is the memory order.  Elements at or
+// beyond tlen are invalid and take no rank.
+//
+// rank_stable gives every valid element its position in the tile stably
+// sorted by digit: first per-warp digit counts (shared-memory atomics, order
+// free), a per-digit scan across warps and across digits, then per item a
+// warp multisplit -- lanes OR their bit into a per-warp digit mask, so each
+// lane learns its same-digit peers and counts those below it.
+//
+// Shared memory: wcnt[kWarps*kRadix], wmask[kWarps*kRadix], dcount[kRadix]
+// (per-digit tile counts), dstart[kRadix] (exclusive prefix), scratch[kWarps].
+// ---------------------------------------------------------------------------
+struct RankSmem {
+    uint32_t wcnt[kWarps * kRadix];
+    uint32_t wmask[kWarps * kRadix];
+    uint32_t dcount[kRadix];
+    uint32_t dstart[kRadix];
+    uint32_t scratch[kWarps];
+};
+
+template <int ITEMS>
+__device__ __forceinline__ void rank_stable(const uint32_t (&dig)[ITEMS], int tlen,
+                                            uint32_t (&rank)[ITEMS], RankSmem &s) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const uint32_t lt = lanemask_lt();
+    uint32_t *wc = s.wcnt + w * kRadix;
+    uint32_t *wm = s.wmask + w * kRadix;
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) {
+        s.wcnt[i] = 0;
+        s.wmask[i] = 0;
+    }
+    __syncthreads();
+    // early counts
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int idx = w * 32 * ITEMS + j * 32 + lane;
+        const bool valid = idx < tlen;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dig[j], 0);
+        if (__all_sync(0xffffffffu, valid && dig[j] == d0)) {
+            if (lane == 0) atomicAdd(&wc[d0], 32u);
+        } else if (valid) {
+            atomicAdd(&wc[dig[j]], 1u);
+        }
+    }
+    __syncthreads();
+    // per digit: exclusive scan over warps, then over digits
+    {
+        const int d = tid;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ww++) {
+            uint32_t c = s.wcnt[ww * kRadix + d];
+            s.wcnt[ww * kRadix + d] = run;
+            run += c;
+        }
+        s.dcount[d] = run;
+        uint32_t total;
+        const uint32_t start = block_exclusive_scan(run, s.scratch, &total);
+        s.dstart[d] = start;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ww++) s.wcnt[ww * kRadix + d] += start;
+    }
+    __syncthreads();
+    // stable multisplit within each warp, item by item
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int idx = w * 32 * ITEMS + j * 32 + lane;
+        const bool valid = idx < tlen;
+        const uint32_t d = dig[j];
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        if (__all_sync(0xffffffffu, valid && d == d0)) {
+            const uint32_t c = wc[d0];
+            rank[j] = c + lane;
+            __syncwarp();
+            if (lane == 0) wc[d0] = c + 32;
+            __syncwarp();
+        } else {
+            if (valid) atomicOr(&wm[d], 1u << lane);
+            __syncwarp();
+            uint32_t peers = 0, c = 0;
+            if (valid) {
+                peers = wm[d];
+                c = wc[d];
+                rank[j] = c + __popc(peers & lt);
+            }
+            __syncwarp();
+            if (valid && (peers >> lane) == 1u) {
+                wc[d] = c + __popc(peers);
+                wm[d] = 0;
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// rank_unstable: positions in the tile grouped by digit, arbitrary order
+// within a digit (enough for keys without payloads, where equal digits are
+// re-sorted by later passes and equal keys are indistinguishable).
+template <int ITEMS>
+__device__ __forceinline__ void rank_unstable(const uint32_t (&dig)[ITEMS], int tlen,
+                                              uint32_t (&rank)[ITEMS], RankSmem &s) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    s.dcount[tid] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        const int idx = w * 32 * ITEMS + j * 32 + lane;
+        const bool valid = idx < tlen;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, dig[j], 0);
+        if (__all_sync(0xffffffffu, valid && dig[j] == d0)) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&s.dcount[d0], 32u);
+            rank[j] = __shfl_sync(0xffffffffu, c, 0) + lane;
+        } else if (valid) {
+            rank[j] = atomicAdd(&s.dcount[dig[j]], 1u);
+        }
+    }
+    __syncthreads();
+    uint32_t total;
+    const uint32_t cnt = s.dcount[tid];
+    const uint32_t start = block_exclusive_scan(cnt, s.scratch, &total);
+    s.dstart[tid] = start;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) rank[j] += s.dstart[dig[j]];
+}
+
+// ---------------------------------------------------------------------------
+// init: resets the counters and seeds level 0 with the whole array, or the
+// finisher with it when it is small.  One thread.
+// ---------------------------------------------------------------------------
+static __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0, int seed_list) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    Counters *c = ws.ctr;
+    c->status = 0;
+    c->njobs = 0;
+    c->alloc[0] = 0;
+    c->alloc[1] = 0;
+    c->copy_alloc = 0;
+    c->ticket_hist = c->ticket_part = c->ticket_fin = c->ticket_copy = c->ticket_prep = 0;
+    if (!seed_list) return;
+    if (n > cutoff) {
+        Bucket b;
+        b.begin = 0;
+        b.len = (uint32_t)n;
+        b.tile_start = 0;
+        b.pos = (uint16_t)pos0;
+        b.buf = 0;
+        b.flags = 0;
+        b.pad = 0;
+        ws.list[0][0] = b;
+        c->alloc[0] = ((unsigned long long)tiles0 << 32) | 1ull;
+    } else if (n >= 2) {
+        Job j;
+        j.begin = 0;
+        j.len = (uint32_t)n;
+        j.pos = (uint16_t)pos0;
+        j.buf = 0;
+        j.pad = 0;
+        ws.jobs[0] = j;
+        c->njobs = 1;
+    }
+}
+
+// seed_segments: segment s = [offsets[s], offsets[s+1]) becomes a level-0
+// bucket (more than `cutoff` keys), a finisher job (2..cutoff keys) or
+// nothing (0 or 1 key).
+static __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_segments,
+                                long long n, int cutoff, int tile) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < num_segments;
+         s += stride) {
+        const long long a = offsets[s], b = offsets[s + 1];
+        if (a < 0 || b < a || b > n || b - a > BINAR_MAX_BUCKET_KEYS) {
+            set_status(ws.ctr, BINAR_ERR_INVALID_ARG);
+            continue;
+        }
+        const long long len = b - a;
+        if (len > cutoff) {
+            const uint32_t tiles = (uint32_t)((len + tile - 1) / tile);
+            const unsigned long long got =
+                atomicAdd(&ws.ctr->alloc[0], ((unsigned long long)tiles << 32) | 1ull);
+            const uint32_t bi = (uint32_t)got, t0 = (uint32_t)(got >> 32);
+            if (bi >= ws.mcap || (unsigned long long)t0 + tiles > ws.tcap) {
+                set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                continue;
+            }
+            Bucket bk;
+            bk.begin = a;
+            bk.len = (uint32_t)len;
+            bk.tile_start = t0;
+            bk.pos = 0;
+            bk.buf = 0;
+            bk.flags = 0;
+            bk.pad = 0;
+            ws.list[0][bi] = bk;
+        } else if (len >= 2) {
+            const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
+            if (ji >= ws.jcap) {
+                set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                continue;
+            }
+            Job j;
+            j.begin = a;
+            j.len = (uint32_t)len;
+            j.pos = 0;
+            j.buf = 0;
+            j.pad = 0;
+            ws.jobs[ji] = j;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// prep: for the level whose list sits in `slot`: tile map, cleared look-back
+// cells, cleared histograms and AND/OR accumulators, reset tickets, and an
+// empty list for the next level.
+// ---------------------------------------------------------------------------
+static __global__ void k_prep(Ws ws, int slot) {
+    if (has_error(ws.ctr)) return;
+    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const uint32_t nb = (uint32_t)alloc, nt = (uint32_t)(alloc >> 32);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ws.ctr->ticket_hist = 0;
+        ws.ctr->ticket_part = 0;
+        ws.ctr->alloc[slot ^ 1] = 0;
+    }
+    if (nb == 0 || nb > ws.mcap || nt > ws.tcap) return;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    // cells: nt * kRadix words, as uint4
+    uint4 *cells4 = reinterpret_cast<uint4 *>(ws.cells);
+    const long long ncell4 = (long long)nt * kRadix / 4;
+    for (long long i = gtid; i < ncell4; i += gstride) cells4[i] = make_uint4(0, 0, 0, 0);
+    uint4 *hist4 = reinterpret_cast<uint4 *>(ws.hist[slot]);
+    const long long nhist4 = (long long)nb * kRadix / 4;
+    for (long long i = gtid; i < nhist4; i += gstride) hist4[i] = make_uint4(0, 0, 0, 0);
+    for (long long b = gtid; b < nb; b += gstride) {
+        ws.andor[slot][2 * b] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        ws.andor[slot][2 * b + 1] = make_uint4(0, 0, 0, 0);
+    }
+    // tile map: CTA-per-bucket, threads stride over the bucket's tiles
+    for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
+        const uint32_t t0 = ws.list[slot][b].tile_start;
+        // number of tiles of this bucket = next bucket's start (or nt) - t0
+        const uint32_t t1 = (b + 1 < nb) ? ws.list[slot][b + 1].tile_start : nt;
+        for (uint32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) ws.tilemap[t] = (uint32_t)b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hist: per bucket of the level, counts of the digit at the bucket's bit
+// position and the AND / OR of its encoded keys.  Persistent CTAs take tiles
+// by ticket.
+// ---------------------------------------------------------------------------
+template <int KB>
+__global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
+    using KT = KeyTraits<KB>;
+    using Raw = typename KT::Raw;
+    using Bits = typename KT::Bits;
+    constexpr int T = TileShape<KB>::kTile;
+    __shared__ uint32_t sh[kRadix];
+    __shared__ uint4 sand[kWarps], sor[kWarps];
+    __shared__ uint32_t sticket;
+    if (has_error(ws.ctr)) return;
+    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const uint32_t nt = (uint32_t)(alloc >> 32);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (;;) {
+        if (tid == 0) sticket = atomicAdd(&ws.ctr->ticket_hist, 1u);
+        sh[tid] = 0;
+        __syncthreads();
+        const uint32_t t = sticket;
+        if (t >= nt) break;
+        const uint32_t b = ws.tilemap[t];
+        const Bucket bk = ws.list[slot][b];
+        if (bk.flags & (kHasHist | kSkip)) {
+            __syncthreads();
+            continue;
+        }
+        const long long tb = bk.begin + (long long)(t - bk.tile_start) * T;
+        const int tlen = (int)min((long long)T, bk.begin + (long long)bk.len - tb);
+        const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
+        Bits a = KT::ones(), o = KT::zero();
+        for (int i = tid; i < tlen; i += kThreads) {
+            const Bits x = KT::encode(src[i], p.map);
+            a = a & x;
+            o = o | x;
+            const uint32_t d = KT::digit(x, bk.pos);
+            atomicAdd(&sh[d], 1u);
+        }
+        // AND / OR: warp reduce, then one thread per CTA updates the bucket
+        uint4 pa = KT::pack(a), po = KT::pack(o);
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            pa.x &= __shfl_xor_sync(0xffffffffu, pa.x, o2);
+            pa.y &= __shfl_xor_sync(0xffffffffu, pa.y, o2);
+            pa.z &= __shfl_xor_sync(0xffffffffu, pa.z, o2);
+            pa.w &= __shfl_xor_sync(0xffffffffu, pa.w, o2);
+            po.x |= __shfl_xor_sync(0xffffffffu, po.x, o2);
+            po.y |= __shfl_xor_sync(0xffffffffu, po.y, o2);
+            po.z |= __shfl_xor_sync(0xffffffffu, po.z, o2);
+            po.w |= __shfl_xor_sync(0xffffffffu, po.w, o2);
+        }
+        if (lane == 0) {
+            sand[w] = pa;
+            sor[w] = po;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint4 ra = sand[0], ro = sor[0];
+            for (int i = 1; i < kWarps; i++) {
+                ra.x &= sand[i].x; ra.y &= sand[i].y; ra.z &= sand[i].z; ra.w &= sand[i].w;
+                ro.x |= sor[i].x; ro.y |= sor[i].y; ro.z |= sor[i].z; ro.w |= sor[i].w;
+            }
+            uint32_t *ga = reinterpret_cast<uint32_t *>(&ws.andor[slot][2 * b]);
+            uint32_t *go = reinterpret_cast<uint32_t *>(&ws.andor[slot][2 * b + 1]);
+            atomicAnd(ga + 0, ra.x); atomicAnd(ga + 1, ra.y);
+            atomicAnd(ga + 2, ra.z); atomicAnd(ga + 3, ra.w);
+            atomicOr(go + 0, ro.x); atomicOr(go + 1, ro.y);
+            atomicOr(go + 2, ro.z); atomicOr(go + 3, ro.w);
+        }
+        const uint32_t c = sh[tid];
+        if (c) atomicAdd(&ws.hist[slot][(size_t)b * kRadix + tid], c);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// classify: one CTA per bucket of the level ("Determine Recursive Call on
+// Sub-arrays").  A bucket whose keys are all equal is finished (the base case
+// "end of the bits").  A bucket whose digit is the same for every key passes
+// through to the next level undivided, at the first bit where its keys differ
+// (the paper's pass-through, with the skip-ahead of "Optimize the
+// Algorithm").  Otherwise it is split: the exclusive prefix of its histogram
+// replaces the counts (the partition kernel reads it), and every child
+// becomes a next-level bucket (more than `cutoff` keys and bits left), a
+// finisher job (at most `cutoff` keys, runs of small children merged), or is
+// finished (all bits consumed; copied back if it sits in the workspace).
+// ---------------------------------------------------------------------------
+template <int KB>
+__global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot, int last_level) {
+    using KT = KeyTraits<KB>;
+    using Bits = typename KT::Bits;
+    constexpr int W = KT::kW;
+    constexpr int T = TileShape<KB>::kTile;
+    __shared__ uint32_t scount[kRadix];
+    __shared__ uint32_t sexcl[kRadix];
+    __shared__ uint32_t scratch[kWarps];
+    __shared__ unsigned long long sbase;
+    if (has_error(ws.ctr)) return;
+    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const uint32_t nb = (uint32_t)alloc;
+    const int tid = threadIdx.x;
+    const int next = slot ^ 1;
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        Bucket bk = ws.list[slot][b];
+        const Bits a = KT::unpack(ws.andor[slot][2 * b]);
+        const Bits o = KT::unpack(ws.andor[slot][2 * b + 1]);
+        const int fd = KT::first_diff(a, o);
+        const uint32_t cnt = ws.hist[slot][(size_t)b * kRadix + tid];
+        const int nonzero = __syncthreads_count(cnt != 0);
+        if (fd >= W || nonzero <= 1) {
+            // finished (all keys equal) or pass-through
+            if (tid == 0) {
+                ws.list[slot][b].flags = bk.flags | kSkip;
+                if (fd >= W) {
+                    if (bk.buf == 1) {
+                        const uint32_t tiles = (uint32_t)(((long long)bk.len + T - 1) / T);
+                        const unsigned long long got = atomicAdd(
+                            &ws.ctr->copy_alloc, ((unsigned long long)tiles << 32) | 1ull);
+                        const uint32_t ci = (uint32_t)got;
+                        if (ci >= ws.ccap) {
+                            set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                        } else {
+                            CopyJob cj;
+                            cj.begin = bk.begin;
+                            cj.len = bk.len;
+                            cj.tile_start = (uint32_t)(got >> 32);
+                            ws.copies[ci] = cj;
+                        }
+                    }
+                } else if (last_level) {
+                    set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);  // cannot happen: fd >= w there
+                } else {
+                    const uint32_t tiles = (uint32_t)(((long long)bk.len + T - 1) / T);
+                    const unsigned long long got =
+                        atomicAdd(&ws.ctr->alloc[next], ((unsigned long long)tiles << 32) | 1ull);
+                    const uint32_t bi = (uint32_t)got, t0 = (uint32_t)(got >> 32);
+                    if (bi >= ws.mcap || (unsigned long long)t0 + tiles > ws.tcap) {
+                        set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                    } else {
+                        Bucket nbk = bk;
+                        nbk.pos = (uint16_t)fd;
+                        nbk.tile_start = t0;
+                        nbk.flags = 0;
+                        ws.list[next][bi] = nbk;
+                    }
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // split
+        uint32_t total;
+        const uint32_t excl = block_exclusive_scan(cnt, scratch, &total);
+        scount[tid] = cnt;
+        sexcl[tid] = excl;
+        ws.hist[slot][(size_t)b * kRadix + tid] = excl;
+        const int cpos = bk.pos + kBits;
+        const int cbuf = bk.buf ^ 1;
+        const bool terminal = cpos >= W;
+        const bool large = !terminal && cnt > (uint32_t)p.cutoff;
+        const uint32_t tiles = large ? (cnt + T - 1) / T : 0;
+        // reserve the large children in the next list, in digit order
+        uint32_t nlarge, ntiles;
+        const uint32_t li = block_exclusive_scan(large ? 1u : 0u, scratch, &nlarge);
+        const uint32_t ti = block_exclusive_scan(tiles, scratch, &ntiles);
+        if (tid == 0) {
+            sbase = nlarge ? atomicAdd(&ws.ctr->alloc[next],
+                                       ((unsigned long long)ntiles << 32) | nlarge)
+                           : 0ull;
+        }
+        __syncthreads();
+        if (large) {
+            const uint32_t bi = (uint32_t)sbase + li;
+            const uint32_t t0 = (uint32_t)(sbase >> 32) + ti;
+            if (bi >= ws.mcap || (unsigned long long)t0 + tiles > ws.tcap) {
+                set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+            } else {
+                Bucket nbk;
+                nbk.begin = bk.begin + excl;
+                nbk.len = cnt;
+                nbk.tile_start = t0;
+                nbk.pos = (uint16_t)cpos;
+                nbk.buf = (uint8_t)cbuf;
+                nbk.flags = 0;
+                nbk.pad = 0;
+                ws.list[next][bi] = nbk;
+            }
+        }
+        // small and finished children: runs, by one thread in digit order
+        if (tid == 0) {
+            const uint32_t C = (uint32_t)p.cutoff;
+            const uint32_t own = C / 8;       // a child this large is a job of its own
+            long long run_begin = -1;
+            uint32_t run_len = 0, run_children = 0, run_child_pos = 0;
+            auto emit = [&](long long begin, uint32_t len, uint32_t children) {
+                if (len == 0) return;
+                int jpos = terminal ? W : (children == 1 ? cpos : bk.pos);
+                if (terminal && cbuf == 0) return;          // finished in place
+                if (!terminal && len == 1 && cbuf == 0) return;
+                const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
+                if (ji >= ws.jcap) {
+                    set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                    return;
+                }
+                Job j;
+                j.begin = begin;
+                j.len = len;
+                j.pos = (uint16_t)jpos;
+                j.buf = (uint8_t)cbuf;
+                j.pad = 0;
+                ws.jobs[ji] = j;
+            };
+            (void)run_child_pos;
+            for (int d = 0; d < kRadix; d++) {
+                const uint32_t c = scount[d];
+                if (c == 0) continue;
+                const long long cb = bk.begin + sexcl[d];
+                const bool big = !terminal && c > C;
+                if (terminal && c > C) {
+                    // finished and large: copy job if it sits in the workspace
+                    emit(run_begin, run_len, run_children);
+                    run_begin = -1; run_len = 0; run_children = 0;
+                    if (cbuf == 1) {
+                        const uint32_t tl = (c + T - 1) / T;
+                        const unsigned long long got = atomicAdd(
+                            &ws.ctr->copy_alloc, ((unsigned long long)tl << 32) | 1ull);
+                        const uint32_t ci = (uint32_t)got;
+                        if (ci >= ws.ccap) {
+                            set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                        } else {
+                            CopyJob cj;
+                            cj.begin = cb;
+                            cj.len = c;
+                            cj.tile_start = (uint32_t)(got >> 32);
+                            ws.copies[ci] = cj;
+                        }
+                    }
+                    continue;
+                }
+                if (big) {
+                    emit(run_begin, run_len, run_children);
+                    run_begin = -1; run_len = 0; run_children = 0;
+                    continue;
+                }
+                if (c >= own) {
+                    emit(run_begin, run_len, run_children);
+                    run_begin = -1; run_len = 0; run_children = 0;
+                    emit(cb, c, 1);
+                    continue;
+                }
+                if (run_begin >= 0 && run_len + c <= C) {
+                    run_len += c;
+                    run_children += 1;
+                } else {
+                    emit(run_begin, run_len, run_children);
+                    run_begin = cb;
+                    run_len = c;
+                    run_children = 1;
+                }
+            }
+            emit(run_begin, run_len, run_children);
+        }
+        __syncthreads();
+    }
+}
+
+// For binar_partition_pass: exclusive prefix of the single bucket's histogram
+// (kept for the partition kernel) and the caller's group offsets.
+static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long long *offsets, long long n) {
+    __shared__ uint32_t scratch[kWarps];
+    const int tid = threadIdx.x;
+    const uint32_t cnt = ws.hist[0][tid];
+    uint32_t total;
+    const uint32_t excl = block_exclusive_scan(cnt, scratch, &total);
+    ws.hist[0][tid] = excl;
+    if (offsets) {
+        offsets[tid] = excl;
+        if (tid == 0) offsets[kRadix] = n;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// partition: one tile per ticket.  The tile's keys (and payloads) are loaded
+// warp-striped, ranked by digit in shared memory, reordered there so that the
+// global writes of every digit run are contiguous, and placed after the
+// tile's predecessors in the same bucket through a single-pass decoupled
+// look-back: every tile publishes its per-digit count (flag AGGREGATE) as
+// soon as it is ranked and its inclusive prefix (flag INCLUSIVE) once known;
+// a tile sums its predecessors' cells back to the first INCLUSIVE one.
+// Cell encoding: 0 = not ready, value+1 in bits 0..30, bit 31 = INCLUSIVE.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kInclusive = 0x80000000u;
+
+template <int KB, int VB, bool STABLE>
+struct PartitionSmem {
+    static constexpr int T = TileShape<KB>::kTile;
+    RankSmem rank;
+    long long offs[kRadix];
+    uint32_t ticket;
+    alignas(16) unsigned char keys[T * KB];
+    alignas(16) unsigned char vals[VB ? T * VB : 16];
+};
+
+template <int KB, int VB, bool STABLE>
+__global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slot, int level,
+                                                        void *keys0, void *keys1, void *vals0,
+                                                        void *vals1) {
+    using KT = KeyTraits<KB>;
+    using Raw = typename KT::Raw;
+    using V = typename ValTraits<VB>::T;
+    constexpr int ITEMS = TileShape<KB>::kItems;
+    constexpr int T = TileShape<KB>::kTile;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE> *>(smem_raw);
+    Raw *skeys = reinterpret_cast<Raw *>(s.keys);
+    V *svals = reinterpret_cast<V *>(s.vals);
+    if (has_error(ws.ctr)) return;
+    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const uint32_t nt = (uint32_t)(alloc >> 32);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (;;) {
+        if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
+        __syncthreads();
+        const uint32_t t = s.ticket;
+        __syncthreads();
+        if (t >= nt) break;
+        const uint32_t b = ws.tilemap[t];
+        const Bucket bk = ws.list[slot][b];
+        if (bk.flags & kSkip) continue;
+        const uint32_t ti = t - bk.tile_start;
+        const long long tb = bk.begin + (long long)ti * T;
+        const long long bend = bk.begin + (long long)bk.len;
+        const int tlen = (int)min((long long)T, bend - tb);
+        const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? keys1 : keys0) + tb;
+        const V *vsrc = VB ? reinterpret_cast<const V *>(bk.buf ? vals1 : vals0) + tb : nullptr;
+        Raw *dst = reinterpret_cast<Raw *>(bk.buf ? keys0 : keys1);
+        V *vdst = VB ? reinterpret_cast<V *>(bk.buf ? vals0 : vals1) : nullptr;
+
+        Raw key[ITEMS];
+        V val[VB ? ITEMS : 1];
+        uint32_t dig[ITEMS], rank[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const int idx = w * 32 * ITEMS + j * 32 + lane;
+            if (idx < tlen) {
+                key[j] = src[idx];
+                if (VB) val[VB ? j : 0] = vsrc[idx];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const int idx = w * 32 * ITEMS + j * 32 + lane;
+            dig[j] = idx < tlen ? KT::digit(KT::encode(key[j], p.map), bk.pos) : 0u;
+        }
+        if (STABLE) rank_stable<ITEMS>(dig, tlen, rank, s.rank);
+        else rank_unstable<ITEMS>(dig, tlen, rank, s.rank);
+
+        // publish this tile's counts
+        const uint32_t cnt = s.rank.dcount[tid];
+        uint32_t *cell = ws.cells + (size_t)t * kRadix + tid;
+        const bool hooked = (level == 0 && (int)t == p.skip_publish_tile);
+        if (!hooked) st_relaxed(cell, (ti == 0 ? kInclusive : 0u) | (cnt + 1));
+
+        // reorder into shared memory
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const int idx = w * 32 * ITEMS + j * 32 + lane;
+            if (idx < tlen) {
+                skeys[rank[j]] = key[j];
+                if (VB) svals[rank[j]] = val[VB ? j : 0];
+            }
+        }
+
+        // look-back over the bucket's earlier tiles (thread = digit)
+        uint32_t excl = 0;
+        if (ti > 0) {
+            uint32_t pt = t - 1;
+            for (;;) {
+                const uint32_t *pc = ws.cells + (size_t)pt * kRadix + tid;
+                uint32_t v = ld_relaxed(pc);
+                if (v == 0) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    while ((v = ld_relaxed(pc)) == 0) {
+                        __nanosleep(64);
+                        if ((long long)(globaltimer_ns() - t0) > p.timeout_ns) {
+                            set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
+                            v = kInclusive | 1u;
+                            break;
+                        }
+                    }
+                }
+                excl += (v & ~kInclusive) - 1;
+                if ((v & kInclusive) || pt == bk.tile_start) break;
+                pt--;
+            }
+            if (!hooked) st_relaxed(cell, kInclusive | (excl + cnt + 1));
+        }
+        s.offs[tid] = bk.begin + (long long)ws.hist[slot][(size_t)b * kRadix + tid] + excl -
+                      (long long)s.rank.dstart[tid];
+        __syncthreads();
+
+        // coalesced write-out of the digit runs
+#pragma unroll 4
+        for (int r = 0; r < ITEMS; r++) {
+            const int i = r * kThreads + tid;
+            if (i < tlen) {
+                const Raw k = skeys[i];
+                const uint32_t d = KT::digit(KT::encode(k, p.map), bk.pos);
+                const long long at = s.offs[d] + i;
+                if (at >= bk.begin && at < bend) {
+                    dst[at] = k;
+                    if (VB) vdst[at] = svals[i];
+                } else {
+                    set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finish: one small bucket (job) per ticket, sorted inside shared memory on
+// bits pos .. w-1 by a stable LSD radix sort over 8-bit windows (the last
+// window starts at pos and may overlap the one below it); windows whose bits
+// are equal across the bucket are skipped.  Keys are written to the caller's
+// key array, payloads gathered from the job's buffer by original index.
+// ---------------------------------------------------------------------------
+template <int KB, int VB>
+struct FinishSmem {
+    static constexpr int T = TileShape<KB>::kTile;
+    RankSmem rank;
+    uint4 sand[kWarps], sor[kWarps];
+    uint32_t ticket;
+    alignas(16) unsigned char keys[T * KB];
+    uint16_t idx[T];
+};
+
+template <int KB, int VB>
+__global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys0, void *keys1,
+                                                     void *vals0, void *vals1) {
+    using KT = KeyTraits<KB>;
+    using Raw = typename KT::Raw;
+    using Bits = typename KT::Bits;
+    using V = typename ValTraits<VB>::T;
+    constexpr int ITEMS = TileShape<KB>::kItems;
+    constexpr int W = KT::kW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &s = *reinterpret_cast<FinishSmem<KB, VB> *>(smem_raw);
+    Raw *skeys = reinterpret_cast<Raw *>(s.keys);
+    if (has_error(ws.ctr)) return;
+    const uint32_t njobs = min(ws.ctr->njobs, ws.jcap);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    for (;;) {
+        if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_fin, 1u);
+        __syncthreads();
+        const uint32_t jt = s.ticket;
+        __syncthreads();
+        if (jt >= njobs) break;
+        const Job job = ws.jobs[jt];
+        const int len = (int)job.len;
+        const Raw *src = reinterpret_cast<const Raw *>(job.buf ? keys1 : keys0) + job.begin;
+        Raw *dst = reinterpret_cast<Raw *>(keys0) + job.begin;
+        const V *vsrc = VB ? reinterpret_cast<const V *>(job.buf ? vals1 : vals0) + job.begin : nullptr;
+        V *vdst = VB ? reinterpret_cast<V *>(vals0) + job.begin : nullptr;
+        if (job.pos >= W || len <= 1) {
+            if (job.buf == 1) {
+                for (int i = tid; i < len; i += kThreads) {
+                    dst[i] = src[i];
+                    if (VB) vdst[i] = vsrc[i];
+                }
+            }
+            continue;
+        }
+        Raw key[ITEMS];
+        uint32_t ix[ITEMS], dig[ITEMS], rank[ITEMS];
+        Bits a = KT::ones(), o = KT::zero();
+#pragma unroll
+        for (int j = 0; j < ITEMS; j++) {
+            const int i = w * 32 * ITEMS + j * 32 + lane;
+            ix[j] = (uint32_t)i;
+            if (i < len) {
+                key[j] = src[i];
+                const Bits x = KT::encode(key[j], p.map);
+                a = a & x;
+                o = o | x;
+            }
+        }
+        uint4 pa = KT::pack(a), po = KT::pack(o);
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            pa.x &= __shfl_xor_sync(0xffffffffu, pa.x, o2);
+            pa.y &= __shfl_xor_sync(0xffffffffu, pa.y, o2);
+            pa.z &= __shfl_xor_sync(0xffffffffu, pa.z, o2);
+            pa.w &= __shfl_xor_sync(0xffffffffu, pa.w, o2);
+            po.x |= __shfl_xor_sync(0xffffffffu, po.x, o2);
+            po.y |= __shfl_xor_sync(0xffffffffu, po.y, o2);
+            po.z |= __shfl_xor_sync(0xffffffffu, po.z, o2);
+            po.w |= __shfl_xor_sync(0xffffffffu, po.w, o2);
+        }
+        if (lane == 0) {
+            s.sand[w] = pa;
+            s.sor[w] = po;
+        }
+        __syncthreads();
+        uint4 ra = s.sand[0], ro = s.sor[0];
+        for (int i = 1; i < kWarps; i++) {
+            ra.x &= s.sand[i].x; ra.y &= s.sand[i].y; ra.z &= s.sand[i].z; ra.w &= s.sand[i].w;
+            ro.x |= s.sor[i].x; ro.y |= s.sor[i].y; ro.z |= s.sor[i].z; ro.w |= s.sor[i].w;
+        }
+        const Bits diff_a = KT::unpack(ra), diff_o = KT::unpack(ro);
+        // LSD over windows [q, q+8): q = w-8, w-16, ... while q > pos, then q = pos
+        int q = W - kBits;
+        bool moved = false;
+        for (;;) {
+            const int qq = q > (int)job.pos ? q : (int)job.pos;
+            // skip a window whose bits are equal across the bucket
+            const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
+            if (varies) {
+                if (moved) {
+                    __syncthreads();
+#pragma unroll
+                    for (int j = 0; j < ITEMS; j++) {
+                        const int i = w * 32 * ITEMS + j * 32 + lane;
+                        if (i < len) {
+                            key[j] = skeys[i];
+                            ix[j] = s.idx[i];
+                        }
+                    }
+                    __syncthreads();
+                }
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    const int i = w * 32 * ITEMS + j * 32 + lane;
+                    dig[j] = i < len ? KT::digit(KT::encode(key[j], p.map), qq) : 0u;
+                }
+                rank_stable<ITEMS>(dig, len, rank, s.rank);
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    const int i = w * 32 * ITEMS + j * 32 + lane;
+                    if (i < len) {
+                        skeys[rank[j]] = key[j];
+                        s.idx[rank[j]] = (uint16_t)ix[j];
+                    }
+                }
+                moved = true;
+            }
+            if (qq == (int)job.pos) break;
+            q -= kBits;
+        }
+        __syncthreads();
+        if (!moved) {
+            // already in order: only a move from the workspace, if any
+            if (job.buf == 1) {
+                for (int i = tid; i < len; i += kThreads) {
+                    dst[i] = src[i];
+                    if (VB) vdst[i] = vsrc[i];
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        // gather payloads first (the job may sit in the caller's arrays)
+        V gv[VB ? ITEMS : 1];
+        if (VB) {
+#pragma unroll
+            for (int r = 0; r < ITEMS; r++) {
+                const int i = r * kThreads + tid;
+                if (i < len) gv[VB ? r : 0] = vsrc[s.idx[i]];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++) {
+            const int i = r * kThreads + tid;
+            if (i < len) {
+                dst[i] = skeys[i];
+                if (VB) vdst[i] = gv[VB ? r : 0];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// copy: finished buckets larger than the cutoff that sit in the workspace
+// arrays go back to the caller's arrays.  Tiles by ticket; the job of a tile is
+// found by binary search on tile_start (increasing with the job index).
+// ---------------------------------------------------------------------------
+template <int KB, int VB>
+__global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *keys1, void *vals0,
+                                                   void *vals1) {
+    using Raw = typename KeyTraits<KB>::Raw;
+    using V = typename ValTraits<VB>::T;
+    constexpr int T = TileShape<KB>::kTile;
+    __shared__ uint32_t sticket;
+    if (has_error(ws.ctr)) return;
+    const unsigned long long ca = ws.ctr->copy_alloc;
+    const uint32_t nj = min((uint32_t)ca, ws.ccap), nt = (uint32_t)(ca >> 32);
+    for (;;) {
+        if (threadIdx.x == 0) sticket = atomicAdd(&ws.ctr->ticket_copy, 1u);
+        __syncthreads();
+        const uint32_t t = sticket;
+        __syncthreads();
+        if (t >= nt || nj == 0) break;
+        uint32_t lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) / 2;
+            if (ws.copies[mid].tile_start <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const CopyJob cj = ws.copies[lo];
+        const long long a = cj.begin + (long long)(t - cj.tile_start) * T;
+        const long long e = min(a + T, cj.begin + (long long)cj.len);
+        const Raw *src = reinterpret_cast<const Raw *>(keys1);
+        Raw *dst = reinterpret_cast<Raw *>(keys0);
+        for (long long i = a + threadIdx.x; i < e; i += kThreads) {
+            dst[i] = src[i];
+            if (VB) reinterpret_cast<V *>(vals0)[i] = reinterpret_cast<const V *>(vals1)[i];
+        }
+    }
+}
+
+}  // namespace binar

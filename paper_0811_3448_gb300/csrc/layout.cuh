@@ -1,0 +1,141 @@
+// layout.cuh -- host-side declarations shared by the C ABI (binar.cu) and the
+// per-key-width level loops (keys*.cu): workspace layout, the description of
+// one call, profiling hooks.
+#pragma once
+
+#include <string>
+
+#include "binar_internal.cuh"
+
+namespace binar {
+
+// ---------------------------------------------------------------------------
+// Host utilities implemented in binar.cu.
+// ---------------------------------------------------------------------------
+int device_sms();                                            // SMs of the current device
+int kernel_ctas_per_sm(const void *fn, size_t smem);         // occupancy (cached per device)
+bool profiling_on();
+void profile_record(const std::string &name, cudaEvent_t a, cudaEvent_t b);
+cudaEvent_t profile_event();
+
+// Launches `f` (which enqueues one kernel) bracketed by profiling events.
+template <typename F>
+int launch(const char *name, int index, cudaStream_t s, F &&f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    const bool prof = profiling_on();
+    if (prof) {
+        a = profile_event();
+        cudaEventRecord(a, s);
+    }
+    f();
+    if (cudaGetLastError() != cudaSuccess) return BINAR_ERR_CUDA;
+    if (prof) {
+        b = profile_event();
+        cudaEventRecord(b, s);
+        std::string nm(name);
+        if (index >= 0) nm += "[" + std::to_string(index) + "]";
+        profile_record(nm, a, b);
+    }
+    return BINAR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.  Capacities are upper bounds for every configuration with
+// a finisher cutoff of at least kMinCutoff:
+//   buckets per level  <= n / (kMinCutoff + 1) + segments + 2  (live buckets exceed the cutoff)
+//   tiles per level    <= n / tile + buckets                   (one ragged tile per bucket)
+//   finisher jobs      <= levels * (19 n / kMinCutoff + 2 * buckets) + segments
+//   copy jobs          <= levels * (n / kMinCutoff + buckets)
+// ---------------------------------------------------------------------------
+constexpr int kMinCutoff = 2048;
+
+inline int tile_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
+inline int levels_for(int kb) { return 8 * kb / kBits; }
+
+struct Layout {
+    size_t ctr, altk, altv, list[2], hist[2], andor[2], tilemap, cells, jobs, copies, total;
+    uint32_t mcap, tcap, jcap, ccap;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline Layout make_layout(long long n, long long segs, int kb, int vb) {
+    Layout L{};
+    const long long T = tile_for(kb), lv = levels_for(kb);
+    const long long m = n / (kMinCutoff + 1) + segs + 2;
+    const long long t = n / T + m + 2;
+    long long j = lv * (19 * (n / kMinCutoff) + 2 * m) + segs + 2;
+    if (j > n + 2) j = n + 2;
+    const long long c = lv * (n / kMinCutoff + m) + 2;
+    L.mcap = (uint32_t)m;
+    L.tcap = (uint32_t)t;
+    L.jcap = (uint32_t)j;
+    L.ccap = (uint32_t)c;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    L.ctr = take(sizeof(Counters));
+    L.altk = take((size_t)n * kb);
+    L.altv = take((size_t)n * vb);
+    for (int s = 0; s < 2; s++) {
+        L.list[s] = take((size_t)m * sizeof(Bucket));
+        L.hist[s] = take((size_t)m * kRadix * sizeof(uint32_t));
+        L.andor[s] = take((size_t)m * 2 * sizeof(uint4));
+    }
+    L.tilemap = take((size_t)t * sizeof(uint32_t));
+    L.cells = take((size_t)t * kRadix * sizeof(uint32_t));
+    L.jobs = take((size_t)j * sizeof(Job));
+    L.copies = take((size_t)c * sizeof(CopyJob));
+    L.total = o;
+    return L;
+}
+
+inline Ws carve(const Layout &L, void *base) {
+    unsigned char *b = static_cast<unsigned char *>(base);
+    Ws ws{};
+    ws.ctr = reinterpret_cast<Counters *>(b + L.ctr);
+    ws.alt_keys = b + L.altk;
+    ws.alt_vals = b + L.altv;
+    for (int s = 0; s < 2; s++) {
+        ws.list[s] = reinterpret_cast<Bucket *>(b + L.list[s]);
+        ws.hist[s] = reinterpret_cast<uint32_t *>(b + L.hist[s]);
+        ws.andor[s] = reinterpret_cast<uint4 *>(b + L.andor[s]);
+    }
+    ws.tilemap = reinterpret_cast<uint32_t *>(b + L.tilemap);
+    ws.cells = reinterpret_cast<uint32_t *>(b + L.cells);
+    ws.jobs = reinterpret_cast<Job *>(b + L.jobs);
+    ws.copies = reinterpret_cast<CopyJob *>(b + L.copies);
+    ws.mcap = L.mcap;
+    ws.tcap = L.tcap;
+    ws.jcap = L.jcap;
+    ws.ccap = L.ccap;
+    return ws;
+}
+
+// ---------------------------------------------------------------------------
+// One call.
+// ---------------------------------------------------------------------------
+struct Call {
+    // sort mode: keys/vals are sorted in place; pass mode: in -> out
+    void *keys, *vals;
+    const void *keys_in, *vals_in;
+    void *keys_out, *vals_out;
+    long long *pass_offsets;
+    int pass_pos;
+    bool pass_mode;
+    const long long *offsets;      // segmented: device offsets, else nullptr
+    long long num_segments;
+    long long n;
+    int map, vb;
+    int cutoff;
+    int ctas_per_sm;
+    long long timeout_ns;
+    int skip_publish_tile;
+    void *ws;
+    cudaStream_t stream;
+};
+
+}  // namespace binar

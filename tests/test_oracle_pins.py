@@ -217,3 +217,29 @@ def test_partition_pass_invariants(dtype, key_map, pos, k):
     assert np.array_equal(offs, np.concatenate([[0], np.cumsum(hist)]))
     d_out = digit[vo.astype(np.int64)]
     assert np.all(np.diff(d_out) >= 0)
+
+
+# ------------------------------------------------------------- rank by definition
+@pytest.mark.parametrize("dtype,key_map", [(np.uint32, MAP_UNSIGNED), (np.int64, MAP_SIGNED),
+                                           (np.float32, MAP_FLOAT)])
+def test_rank_of_matches_searchsorted(dtype, key_map):
+    g = np.random.Generator(np.random.PCG64(21))
+    if dtype == np.float32:
+        keys = inputs.config3_f32(3000)
+        keys = keys[~np.isnan(keys)]
+    else:
+        keys = inputs.uniform_keys(3000, dtype, g) % dtype(50)
+    s = np.sort(keys)
+    for probe in list(keys[:40]) + [dtype(7)]:
+        lt, le = oracle.rank_of(keys, np.array([probe], dtype=dtype), key_map)
+        if dtype == np.float32 and probe == 0:
+            continue  # +0 and -0 are distinct keys here, equal for numpy
+        assert lt == np.searchsorted(s, probe, side="left")
+        assert le == np.searchsorted(s, probe, side="right")
+
+
+def test_occurrence_finds_the_jth_copy():
+    keys = np.array([5, 3, 5, 5, 1, 3], dtype=np.uint32)
+    five = np.array([5], dtype=np.uint32)
+    assert [oracle.occurrence(keys, five, j) for j in range(4)] == [0, 2, 3, -1]
+    assert oracle.occurrence(keys, np.array([1], dtype=np.uint32), 0) == 4
