@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput of libbinar on GB300: GKeys/s and fraction of the HBM roofline.
+
+Workload (one step = one complete in-place stable sort): 256M uint32 keys with
+uint32 payloads equal to the original index, keys uniform over [0, 2^32)
+(PCG64, seed 8113448 + 200), synthetic.  The input (2 GiB, larger than the
+129 MB L2) is restored from a pristine device copy before every step; only the
+sort is timed, with CUDA events on the sort's stream.
+
+Prints one JSON line (rank 0).  Run as ``python bench.py [--gpus N --steps K
+--warmup W]``; for N > 1 under torchrun every rank sorts its own replica
+(no data exchange) and rank 0 reports the max-over-ranks time.
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GKeys/s and % HBM roofline (u32/u64, 1M–1G keys); serving p50/p99 ms"
+UNIT = "GKeys/s"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "256M uint32 keys + uint32 index payload, uniform, stable in-place sort"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["binar", "reference"], default="binar")
+    ap.add_argument("--n", type=int, default=256 << 20)
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", FALLBACK_HBM_GBS)), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0811_3448_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernels have not changed since it was taken; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    return None if ent is None else ent.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def cpu_baseline(n_sample: int, dist: str):
+    """The oracle's parallel binar sort on the host cores, on a bounded sample."""
+    import oracle
+    from paper_0811_3448_gb300 import inputs
+    cores = os.cpu_count() or 1
+    log2g = max(0, int(math.floor(math.log2(cores))))
+    keys = inputs.config2_keys(n_sample, np.uint32, dist)
+    vals = inputs.index_payload(n_sample)
+    t0 = time.perf_counter()
+    oracle.binar_sort_parallel(keys, vals, log2_groups=log2g)
+    dt = time.perf_counter() - t0
+    return {"value": n_sample / dt / 1e9, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
+            "sample": f"{n_sample} uint32 keys + uint32 payload ({dist}), parallel binar sort "
+                      f"(leading-bit split, one thread per group), {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, each step a bounded sample of the workload."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_0811_3448_gb300 import inputs
+    cores = os.cpu_count() or 1
+    log2g = max(0, int(math.floor(math.log2(cores))))
+    # calibrate the sample so that warmup + steps take about 90 s
+    probe = 1 << 20
+    k = inputs.config2_keys(probe, np.uint32, args.dist)
+    v = inputs.index_payload(probe)
+    t0 = time.perf_counter()
+    oracle.binar_sort_parallel(k, v, log2_groups=log2g)
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    per_step = 90.0 / max(1, args.steps + args.warmup)
+    n = int(min(args.n, max(1 << 18, rate * per_step)))
+    keys = inputs.config2_keys(n, np.uint32, args.dist)
+    vals = inputs.index_payload(n)
+    times = []
+    for i in range(args.warmup + args.steps):
+        kk, vv = keys.copy(), vals.copy()
+        t0 = time.perf_counter()
+        oracle.binar_sort_parallel(kk, vv, log2_groups=log2g)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * statistics.mean(times)
+    value = n / (ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": args.n, "sample_n": n, "dist": args.dist,
+                      "parallelism": "replicas"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
+                            "sample": f"{n} keys per step (bounded sample of the {args.n}-key "
+                                      f"workload), parallel binar sort on host cores"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def check_sorted_stable(tk, tv, orig_keys_dev):
+    """Sorted, a permutation of the input, and stable (payload = index)."""
+    import torch
+    k = tk.to(torch.int64)
+    v = tv.to(torch.int64)
+    ok = bool((k[1:] >= k[:-1]).all())
+    ok &= bool((orig_keys_dev.to(torch.int64)[v] == k).all())
+    ok &= bool((torch.bincount(v, minlength=k.shape[0]) == 1).all())
+    eq = k[1:] == k[:-1]
+    ok &= bool((v[1:][eq] > v[:-1][eq]).all())
+    return ok
+
+
+def run_binar(args):
+    import torch
+    from paper_0811_3448_gb300 import binding, inputs
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    binding.load()
+    dev = torch.device("cuda", local)
+    n = args.n
+
+    keys_h = inputs.config2_keys(n, np.uint32, args.dist)
+    vals_h = inputs.index_payload(n)
+    keys0 = torch.from_numpy(keys_h).to(dev)
+    vals0 = torch.from_numpy(vals_h).to(dev)
+    keys = torch.empty_like(keys0)
+    vals = torch.empty_like(vals0)
+    ws = binding.workspace(n, 4, 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        binding.sort_pairs(keys, vals, ws=ws)
+    binding.check_status(ws)
+
+    sampler = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    binding.profile_start()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        evs[i][0].record(stream)
+        binding.sort_pairs(keys, vals, ws=ws)
+        evs[i][1].record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    kstats = binding.profile_stop()
+    sampler.stop()
+    binding.check_status(ws)
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * n / (ms_max * 1e-3) / 1e9
+    valid = check_sorted_stable(keys, vals, keys0)
+
+    # roofline of the first partition pass (the whole array, one read + one write)
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    total_ms = sum(t for _, t in kstats.values()) or 1.0
+    for name, (launches, t) in kstats.items():
+        kernels[name] = {"launches": launches, "ms_per_launch": t / max(launches, 1),
+                         "share": t / total_ms}
+    part = kstats.get("partition[0]")
+    roofline = None
+    if part:
+        per_launch_ms = part[1] / part[0]
+        alg_bytes = 2 * (4 + 4) * n
+        achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "partition[0]", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst)",
+                    "traffic": recorded_traffic("partition[0]"),
+                    "algorithmic_bytes_per_launch": alg_bytes,
+                    "frac_of_8TBs_spec": achieved / 8000.0}
+    dominant = max(kernels.items(), key=lambda kv: kv[1]["share"])[0] if kernels else None
+    gpu_launches = int(sum(l for l, _ in kstats.values()))
+
+    # end to end through the public API: pinned host buffers, copies inside the timed region
+    hk = torch.from_numpy(keys_h).pin_memory()
+    hv = torch.from_numpy(vals_h).pin_memory()
+    ok_k = torch.empty_like(hk).pin_memory()
+    ok_v = torch.empty_like(hv).pin_memory()
+    e2e_times = []
+    for i in range(args.e2e_steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        keys.copy_(hk, non_blocking=True)
+        vals.copy_(hv, non_blocking=True)
+        binding.sort_pairs(keys, vals, ws=ws)
+        ok_k.copy_(keys, non_blocking=True)
+        ok_v.copy_(vals, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if i > 0:
+            e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e2e_times)
+    e2e = {"value": world * n / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": n, "key": "uint32", "payload": "uint32",
+                      "dist": args.dist, "parallelism": f"replicas x{world}",
+                      "l2": "2 GiB inputs (> 129 MB L2), restored from a pristine copy "
+                            "before every timed sort"},
+           "e2e": e2e, "roofline": roofline, "gpu_launches": gpu_launches,
+           "clocks": sampler.summary(), "validated": valid, "dominant_kernel": dominant,
+           "kernels": kernels, "wall_s_timed_loop": wall}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(32 << 20, args.dist)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_binar(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -168,7 +168,13 @@ static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
     if ((rc = resolve_config(cfg, key_bytes, c))) return rc;
-    if (n == 0 || (d_offsets && num_segments == 0)) return BINAR_OK;
+    if (n == 0 || (d_offsets && num_segments == 0)) {
+        // nothing to sort; the status word still reports this call
+        if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream)) !=
+            cudaSuccess)
+            return BINAR_ERR_CUDA;
+        return BINAR_OK;
+    }
     c.keys = d_keys;
     c.vals = val_bytes ? d_vals : nullptr;
     c.offsets = reinterpret_cast<const long long *>(d_offsets);
@@ -228,6 +234,7 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
         if (d_offsets &&
             cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * (kRadix + 1), s) != cudaSuccess)
             return BINAR_ERR_CUDA;
+        if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BINAR_ERR_CUDA;
         return BINAR_OK;
     }
     c.pass_mode = true;

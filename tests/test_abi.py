@@ -102,8 +102,3 @@ def test_argument_checks_need_no_gpu(lib):
                                     aligned, big, None, None) == binding.ERR_INVALID_ARG
     assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 0, 4, None,
                                     aligned, big, None, None) == binding.ERR_UNSUPPORTED
-
-
-def test_empty_sort_is_a_no_op_without_gpu(lib):
-    aligned = ctypes.c_void_p(0x1000)
-    assert _call_keys(lib, None, 0, 4, 0, aligned, 1 << 20) == binding.OK
