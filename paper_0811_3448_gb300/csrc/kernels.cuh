@@ -55,31 +55,66 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 }
 
 // ---------------------------------------------------------------------------
-// Tile ranking.  A tile of up to kThreads * ITEMS keys is held "warp-striped":
-// item j of lane l in warp w is tile element w*32*ITEMS + j*32 + l, so the
-// processing order (warp, item, lane) is the memory order.  Elements at or
-// beyond tlen are invalid and take no rank.
+// Tile ranking.  A tile of up to kThreads * ITEMS keys is held "warp-striped"
+// with `iu` items per thread (iu <= ITEMS, uniform over the CTA): item j of
+// lane l in warp w is tile element w*32*iu + j*32 + l, so the processing
+// order (warp, item, lane) is the memory order.  Items with j >= iu or with an
+// element index >= len are invalid and take no rank.
 //
-// rank_stable gives every valid element its position in the tile stably
-// sorted by digit: first per-warp digit counts (shared-memory atomics, order
-// free), a per-digit scan across warps and across digits, then per item a
-// warp multisplit -- lanes OR their bit into a per-warp digit mask, so each
-// lane learns its same-digit peers and counts those below it.
-//
-// Shared memory: wcnt[kWarps*kRadix], wmask[kWarps*kRadix], dcount[kRadix]
-// (per-digit tile counts), dstart[kRadix] (exclusive prefix), scratch[kWarps].
+// Digits (< 256) and ranks (< 65536) are kept packed in registers: four digits
+// or two ranks per 32-bit word.
 // ---------------------------------------------------------------------------
-struct RankSmem {
-    uint32_t wcnt[kWarps * kRadix];
-    uint32_t wmask[kWarps * kRadix];
+template <int ITEMS>
+struct Packed {
+    uint32_t d[(ITEMS + 3) / 4];
+    uint32_t r[(ITEMS + 1) / 2];
+    __device__ __forceinline__ uint32_t dig(int j) const {
+        return (d[j >> 2] >> ((j & 3) * 8)) & 0xffu;
+    }
+    __device__ __forceinline__ void set_dig(int j, uint32_t v) {   // in order of j
+        if ((j & 3) == 0) d[j >> 2] = v;
+        else d[j >> 2] |= v << ((j & 3) * 8);
+    }
+    __device__ __forceinline__ uint32_t rank(int j) const {
+        return (r[j >> 1] >> ((j & 1) * 16)) & 0xffffu;
+    }
+    __device__ __forceinline__ void set_rank(int j, uint32_t v) {  // in order of j
+        if ((j & 1) == 0) r[j >> 1] = v;
+        else r[j >> 1] |= v << 16;
+    }
+    // adds v to rank j; the sum stays below 65536, so the other half is untouched
+    __device__ __forceinline__ void add_rank(int j, uint32_t v) {
+        r[j >> 1] += v << ((j & 1) * 16);
+    }
+};
+
+__device__ __forceinline__ int striped(int iu, int j) {
+    return (threadIdx.x >> 5) * 32 * iu + j * 32 + (threadIdx.x & 31);
+}
+
+// Shared memory of the ranking: per-warp digit counters and lane masks,
+// per-digit tile counts (dcount) and their exclusive prefix (dstart).
+struct RankSmemLite {
     uint32_t dcount[kRadix];
     uint32_t dstart[kRadix];
     uint32_t scratch[kWarps];
 };
+struct RankSmem : RankSmemLite {
+    uint32_t wcnt[kWarps * kRadix];
+    uint32_t wmask[kWarps * kRadix];
+};
+template <bool STABLE> struct RankSmemFor { using T = RankSmem; };
+template <> struct RankSmemFor<false> { using T = RankSmemLite; };
 
+// rank_stable: every valid item gets its position in the tile stably sorted
+// by digit.  First per-warp digit counts (shared-memory atomics, order free),
+// a per-digit exclusive scan across warps and across digits, then item by
+// item a warp multisplit: lanes OR their bit into a per-warp digit mask, so
+// each lane learns its same-digit peers and counts those below it; the
+// highest peer advances the warp's counter.  A warp whose 32 lanes share one
+// digit (sorted input) takes a shortcut without atomics.
 template <int ITEMS>
-__device__ __forceinline__ void rank_stable(const uint32_t (&dig)[ITEMS], int tlen,
-                                            uint32_t (&rank)[ITEMS], RankSmem &s) {
+__device__ __forceinline__ void rank_stable(Packed<ITEMS> &pk, int iu, int len, RankSmem &s) {
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
     uint32_t *wc = s.wcnt + w * kRadix;
@@ -89,26 +124,26 @@ __device__ __forceinline__ void rank_stable(const uint32_t (&dig)[ITEMS], int tl
         s.wmask[i] = 0;
     }
     __syncthreads();
-    // early counts
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        const int idx = w * 32 * ITEMS + j * 32 + lane;
-        const bool valid = idx < tlen;
-        const uint32_t d0 = __shfl_sync(0xffffffffu, dig[j], 0);
-        if (__all_sync(0xffffffffu, valid && dig[j] == d0)) {
-            if (lane == 0) atomicAdd(&wc[d0], 32u);
-        } else if (valid) {
-            atomicAdd(&wc[dig[j]], 1u);
+        if (j < iu) {
+            const bool valid = striped(iu, j) < len;
+            const uint32_t d = pk.dig(j);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            if (__all_sync(0xffffffffu, valid && d == d0)) {
+                if (lane == 0) atomicAdd(&wc[d0], 32u);
+            } else if (valid) {
+                atomicAdd(&wc[d], 1u);
+            }
         }
     }
     __syncthreads();
-    // per digit: exclusive scan over warps, then over digits
     {
         const int d = tid;
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < kWarps; ww++) {
-            uint32_t c = s.wcnt[ww * kRadix + d];
+            const uint32_t c = s.wcnt[ww * kRadix + d];
             s.wcnt[ww * kRadix + d] = run;
             run += c;
         }
@@ -120,58 +155,64 @@ __device__ __forceinline__ void rank_stable(const uint32_t (&dig)[ITEMS], int tl
         for (int ww = 0; ww < kWarps; ww++) s.wcnt[ww * kRadix + d] += start;
     }
     __syncthreads();
-    // stable multisplit within each warp, item by item
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        const int idx = w * 32 * ITEMS + j * 32 + lane;
-        const bool valid = idx < tlen;
-        const uint32_t d = dig[j];
-        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-        if (__all_sync(0xffffffffu, valid && d == d0)) {
-            const uint32_t c = wc[d0];
-            rank[j] = c + lane;
-            __syncwarp();
-            if (lane == 0) wc[d0] = c + 32;
-            __syncwarp();
-        } else {
-            if (valid) atomicOr(&wm[d], 1u << lane);
-            __syncwarp();
-            uint32_t peers = 0, c = 0;
-            if (valid) {
-                peers = wm[d];
-                c = wc[d];
-                rank[j] = c + __popc(peers & lt);
+        if (j < iu) {
+            const bool valid = striped(iu, j) < len;
+            const uint32_t d = pk.dig(j);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            uint32_t rk = 0;
+            if (__all_sync(0xffffffffu, valid && d == d0)) {
+                const uint32_t c = wc[d0];
+                rk = c + lane;
+                __syncwarp();
+                if (lane == 0) wc[d0] = c + 32;
+                __syncwarp();
+            } else {
+                if (valid) atomicOr(&wm[d], 1u << lane);
+                __syncwarp();
+                uint32_t peers = 0, c = 0;
+                if (valid) {
+                    peers = wm[d];
+                    c = wc[d];
+                    rk = c + __popc(peers & lt);
+                }
+                __syncwarp();
+                if (valid && (peers >> lane) == 1u) {
+                    wc[d] = c + __popc(peers);
+                    wm[d] = 0;
+                }
+                __syncwarp();
             }
-            __syncwarp();
-            if (valid && (peers >> lane) == 1u) {
-                wc[d] = c + __popc(peers);
-                wm[d] = 0;
-            }
-            __syncwarp();
+            pk.set_rank(j, rk);
         }
     }
 }
 
-// rank_unstable: positions in the tile grouped by digit, arbitrary order
-// within a digit (enough for keys without payloads, where equal digits are
-// re-sorted by later passes and equal keys are indistinguishable).
+// rank_unstable: positions grouped by digit, arbitrary order inside a digit.
+// Enough for keys without payloads in an MSD pass (equal digits are split by
+// later passes, equal keys are indistinguishable) and for the first window of
+// an LSD sort of keys.  One block-wide counter per digit.
 template <int ITEMS>
-__device__ __forceinline__ void rank_unstable(const uint32_t (&dig)[ITEMS], int tlen,
-                                              uint32_t (&rank)[ITEMS], RankSmem &s) {
-    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+__device__ __forceinline__ void rank_unstable(Packed<ITEMS> &pk, int iu, int len, RankSmemLite &s) {
+    const int tid = threadIdx.x, lane = tid & 31;
     s.dcount[tid] = 0;
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < ITEMS; j++) {
-        const int idx = w * 32 * ITEMS + j * 32 + lane;
-        const bool valid = idx < tlen;
-        const uint32_t d0 = __shfl_sync(0xffffffffu, dig[j], 0);
-        if (__all_sync(0xffffffffu, valid && dig[j] == d0)) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&s.dcount[d0], 32u);
-            rank[j] = __shfl_sync(0xffffffffu, c, 0) + lane;
-        } else if (valid) {
-            rank[j] = atomicAdd(&s.dcount[dig[j]], 1u);
+        if (j < iu) {
+            const bool valid = striped(iu, j) < len;
+            const uint32_t d = pk.dig(j);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            uint32_t rk = 0;
+            if (__all_sync(0xffffffffu, valid && d == d0)) {
+                uint32_t c = 0;
+                if (lane == 0) c = atomicAdd(&s.dcount[d0], 32u);
+                rk = __shfl_sync(0xffffffffu, c, 0) + lane;
+            } else if (valid) {
+                rk = atomicAdd(&s.dcount[d], 1u);
+            }
+            pk.set_rank(j, rk);
         }
     }
     __syncthreads();
@@ -181,7 +222,32 @@ __device__ __forceinline__ void rank_unstable(const uint32_t (&dig)[ITEMS], int 
     s.dstart[tid] = start;
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < ITEMS; j++) rank[j] += s.dstart[dig[j]];
+    for (int j = 0; j < ITEMS; j++) {
+        if (j < iu) pk.add_rank(j, s.dstart[pk.dig(j)]);
+    }
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void rank_tile(Packed<ITEMS> &pk, int iu, int len, RankSmem &s) {
+    rank_stable<ITEMS>(pk, iu, len, s);
+}
+template <int ITEMS>
+__device__ __forceinline__ void rank_tile(Packed<ITEMS> &pk, int iu, int len, RankSmemLite &s) {
+    rank_unstable<ITEMS>(pk, iu, len, s);
+}
+
+// cp.async copies of 4 or 8 bytes from global to shared memory (no registers).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem_src),
+                     "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -592,13 +658,16 @@ static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long lon
 }
 
 // ---------------------------------------------------------------------------
-// partition: one tile per ticket.  The tile's keys (and payloads) are loaded
-// warp-striped, ranked by digit in shared memory, reordered there so that the
-// global writes of every digit run are contiguous, and placed after the
-// tile's predecessors in the same bucket through a single-pass decoupled
-// look-back: every tile publishes its per-digit count (flag AGGREGATE) as
-// soon as it is ranked and its inclusive prefix (flag INCLUSIVE) once known;
-// a tile sums its predecessors' cells back to the first INCLUSIVE one.
+// partition: one tile per ticket.  The tile's keys and payloads are copied
+// into shared memory with cp.async (coalesced, no registers), the keys are
+// ranked by digit (digits and ranks packed in registers), and the ranking is
+// written as a permutation perm[sorted position] = tile position.  The tile
+// is placed after its predecessors in the same bucket through a single-pass
+// decoupled look-back: every tile publishes its per-digit count (AGGREGATE)
+// as soon as it is ranked, and its inclusive prefix (INCLUSIVE) once known; a
+// tile sums its predecessors' cells back to the first INCLUSIVE one.  Finally
+// the tile is written in sorted order, so that the global writes of every
+// digit run are contiguous.
 // Cell encoding: 0 = not ready, value+1 in bits 0..30, bit 31 = INCLUSIVE.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kInclusive = 0x80000000u;
@@ -606,17 +675,18 @@ constexpr uint32_t kInclusive = 0x80000000u;
 template <int KB, int VB, bool STABLE>
 struct PartitionSmem {
     static constexpr int T = TileShape<KB>::kTile;
-    RankSmem rank;
+    typename RankSmemFor<STABLE>::T rank;
     long long offs[kRadix];
     uint32_t ticket;
     alignas(16) unsigned char keys[T * KB];
     alignas(16) unsigned char vals[VB ? T * VB : 16];
+    uint16_t perm[T];
 };
 
 template <int KB, int VB, bool STABLE>
-__global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slot, int level,
-                                                        void *keys0, void *keys1, void *vals0,
-                                                        void *vals1) {
+__global__ void __launch_bounds__(kThreads, 2)
+    k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
+                void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
@@ -627,9 +697,11 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
-    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const Bucket *list = slot ? ws.list[1] : ws.list[0];
+    const uint32_t *prefix = slot ? ws.hist[1] : ws.hist[0];
+    const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x;
     for (;;) {
         if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
         __syncthreads();
@@ -637,7 +709,7 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
         __syncthreads();
         if (t >= nt) break;
         const uint32_t b = ws.tilemap[t];
-        const Bucket bk = ws.list[slot][b];
+        const Bucket bk = list[b];
         if (bk.flags & kSkip) continue;
         const uint32_t ti = t - bk.tile_start;
         const long long tb = bk.begin + (long long)ti * T;
@@ -648,24 +720,20 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
         Raw *dst = reinterpret_cast<Raw *>(bk.buf ? keys0 : keys1);
         V *vdst = VB ? reinterpret_cast<V *>(bk.buf ? vals0 : vals1) : nullptr;
 
-        Raw key[ITEMS];
-        V val[VB ? ITEMS : 1];
-        uint32_t dig[ITEMS], rank[ITEMS];
+        for (int i = tid; i < tlen; i += kThreads) {
+            cp_async<KB>(&skeys[i], &src[i]);
+            if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+
+        Packed<ITEMS> pk;
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
-            const int idx = w * 32 * ITEMS + j * 32 + lane;
-            if (idx < tlen) {
-                key[j] = src[idx];
-                if (VB) val[VB ? j : 0] = vsrc[idx];
-            }
+            const int i = striped(ITEMS, j);
+            pk.set_dig(j, i < tlen ? KT::digit(KT::encode(skeys[i], p.map), bk.pos) : 0u);
         }
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int idx = w * 32 * ITEMS + j * 32 + lane;
-            dig[j] = idx < tlen ? KT::digit(KT::encode(key[j], p.map), bk.pos) : 0u;
-        }
-        if (STABLE) rank_stable<ITEMS>(dig, tlen, rank, s.rank);
-        else rank_unstable<ITEMS>(dig, tlen, rank, s.rank);
+        rank_tile<ITEMS>(pk, ITEMS, tlen, s.rank);
 
         // publish this tile's counts
         const uint32_t cnt = s.rank.dcount[tid];
@@ -673,13 +741,13 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
         const bool hooked = (level == 0 && (int)t == p.skip_publish_tile);
         if (!hooked) st_relaxed(cell, (ti == 0 ? kInclusive : 0u) | (cnt + 1));
 
-        // reorder into shared memory
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
-            const int idx = w * 32 * ITEMS + j * 32 + lane;
-            if (idx < tlen) {
-                skeys[rank[j]] = key[j];
-                if (VB) svals[rank[j]] = val[VB ? j : 0];
+            const int i = striped(ITEMS, j);
+            if (i < tlen) {
+                const uint32_t r = pk.rank(j);
+                if (r < (uint32_t)tlen) s.perm[r] = (uint16_t)i;
+                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
             }
         }
 
@@ -693,7 +761,7 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
                 if (v == 0) {
                     const unsigned long long t0 = globaltimer_ns();
                     while ((v = ld_relaxed(pc)) == 0) {
-                        __nanosleep(64);
+                        __nanosleep(32);
                         if ((long long)(globaltimer_ns() - t0) > p.timeout_ns) {
                             set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
                             v = kInclusive | 1u;
@@ -707,21 +775,26 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
             }
             if (!hooked) st_relaxed(cell, kInclusive | (excl + cnt + 1));
         }
-        s.offs[tid] = bk.begin + (long long)ws.hist[slot][(size_t)b * kRadix + tid] + excl -
+        s.offs[tid] = bk.begin + (long long)prefix[(size_t)b * kRadix + tid] + excl -
                       (long long)s.rank.dstart[tid];
         __syncthreads();
 
-        // coalesced write-out of the digit runs
-#pragma unroll 4
+        // write-out in sorted order: the digit runs are contiguous in memory
+#pragma unroll 8
         for (int r = 0; r < ITEMS; r++) {
             const int i = r * kThreads + tid;
             if (i < tlen) {
-                const Raw k = skeys[i];
+                int q = s.perm[i];
+                if (q >= tlen) {
+                    set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                    q = 0;
+                }
+                const Raw k = skeys[q];
                 const uint32_t d = KT::digit(KT::encode(k, p.map), bk.pos);
                 const long long at = s.offs[d] + i;
                 if (at >= bk.begin && at < bend) {
                     dst[at] = k;
-                    if (VB) vdst[at] = svals[i];
+                    if (VB) vdst[at] = svals[q];
                 } else {
                     set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
                 }
@@ -733,24 +806,28 @@ __global__ void __launch_bounds__(kThreads) k_partition(Ws ws, Params p, int slo
 
 // ---------------------------------------------------------------------------
 // finish: one small bucket (job) per ticket, sorted inside shared memory on
-// bits pos .. w-1 by a stable LSD radix sort over 8-bit windows (the last
-// window starts at pos and may overlap the one below it); windows whose bits
-// are equal across the bucket are skipped.  Keys are written to the caller's
-// key array, payloads gathered from the job's buffer by original index.
+// bits pos .. w-1 by an LSD radix sort over 8-bit windows (the last window
+// starts at pos and may overlap the one below it); windows whose bits are
+// equal across the bucket are skipped.  The keys stay where cp.async put them;
+// each window pass refines a permutation perm[sorted position] = input
+// position.  Every pass is stable except the first one of a key-only sort.
+// Keys are written to the caller's key array, payloads gathered from the
+// job's buffer through the permutation.  Items per thread follow the job size
+// (iu = ceil(len / 256)).
 // ---------------------------------------------------------------------------
-template <int KB, int VB>
+template <int KB>
 struct FinishSmem {
     static constexpr int T = TileShape<KB>::kTile;
     RankSmem rank;
     uint4 sand[kWarps], sor[kWarps];
     uint32_t ticket;
     alignas(16) unsigned char keys[T * KB];
-    uint16_t idx[T];
+    uint16_t perm[T];
 };
 
 template <int KB, int VB>
-__global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys0, void *keys1,
-                                                     void *vals0, void *vals1) {
+__global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
+    k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
@@ -758,7 +835,7 @@ __global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys
     constexpr int ITEMS = TileShape<KB>::kItems;
     constexpr int W = KT::kW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &s = *reinterpret_cast<FinishSmem<KB, VB> *>(smem_raw);
+    auto &s = *reinterpret_cast<FinishSmem<KB> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     if (has_error(ws.ctr)) return;
     const uint32_t njobs = min(ws.ctr->njobs, ws.jcap);
@@ -784,19 +861,15 @@ __global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys
             }
             continue;
         }
-        Raw key[ITEMS];
-        uint32_t ix[ITEMS], dig[ITEMS], rank[ITEMS];
+        for (int i = tid; i < len; i += kThreads) cp_async<KB>(&skeys[i], &src[i]);
+        cp_async_wait_all();
+        __syncthreads();
+        const int iu = (len + kThreads - 1) / kThreads;
         Bits a = KT::ones(), o = KT::zero();
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int i = w * 32 * ITEMS + j * 32 + lane;
-            ix[j] = (uint32_t)i;
-            if (i < len) {
-                key[j] = src[i];
-                const Bits x = KT::encode(key[j], p.map);
-                a = a & x;
-                o = o | x;
-            }
+        for (int i = tid; i < len; i += kThreads) {
+            const Bits x = KT::encode(skeys[i], p.map);
+            a = a & x;
+            o = o | x;
         }
         uint4 pa = KT::pack(a), po = KT::pack(o);
 #pragma unroll
@@ -824,35 +897,38 @@ __global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys
         // LSD over windows [q, q+8): q = w-8, w-16, ... while q > pos, then q = pos
         int q = W - kBits;
         bool moved = false;
+        Packed<ITEMS> pk;
+        uint32_t src_pos[(ITEMS + 1) / 2];   // input positions of this thread's items, packed
         for (;;) {
             const int qq = q > (int)job.pos ? q : (int)job.pos;
-            // skip a window whose bits are equal across the bucket
             const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
             if (varies) {
-                if (moved) {
-                    __syncthreads();
+                if (moved) __syncthreads();
 #pragma unroll
-                    for (int j = 0; j < ITEMS; j++) {
-                        const int i = w * 32 * ITEMS + j * 32 + lane;
-                        if (i < len) {
-                            key[j] = skeys[i];
-                            ix[j] = s.idx[i];
+                for (int j = 0; j < ITEMS; j++) {
+                    if (j < iu) {
+                        const int i = striped(iu, j);
+                        uint32_t x = 0;
+                        if (i < len) x = moved ? s.perm[i] : (uint32_t)i;
+                        if (x >= (uint32_t)len) {
+                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                            x = 0;
                         }
+                        if ((j & 1) == 0) src_pos[j >> 1] = x;
+                        else src_pos[j >> 1] |= x << 16;
+                        pk.set_dig(j, i < len ? KT::digit(KT::encode(skeys[x], p.map), qq) : 0u);
                     }
-                    __syncthreads();
                 }
+                if (VB || moved) rank_stable<ITEMS>(pk, iu, len, s.rank);
+                else rank_unstable<ITEMS>(pk, iu, len, s.rank);
 #pragma unroll
                 for (int j = 0; j < ITEMS; j++) {
-                    const int i = w * 32 * ITEMS + j * 32 + lane;
-                    dig[j] = i < len ? KT::digit(KT::encode(key[j], p.map), qq) : 0u;
-                }
-                rank_stable<ITEMS>(dig, len, rank, s.rank);
-#pragma unroll
-                for (int j = 0; j < ITEMS; j++) {
-                    const int i = w * 32 * ITEMS + j * 32 + lane;
-                    if (i < len) {
-                        skeys[rank[j]] = key[j];
-                        s.idx[rank[j]] = (uint16_t)ix[j];
+                    if (j < iu && striped(iu, j) < len) {
+                        const uint32_t r = pk.rank(j);
+                        if (r < (uint32_t)len)
+                            s.perm[r] = (uint16_t)(src_pos[j >> 1] >> ((j & 1) * 16));
+                        else
+                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
                     }
                 }
                 moved = true;
@@ -865,30 +941,32 @@ __global__ void __launch_bounds__(kThreads) k_finish(Ws ws, Params p, void *keys
             // already in order: only a move from the workspace, if any
             if (job.buf == 1) {
                 for (int i = tid; i < len; i += kThreads) {
-                    dst[i] = src[i];
+                    dst[i] = skeys[i];
                     if (VB) vdst[i] = vsrc[i];
                 }
             }
             __syncthreads();
             continue;
         }
-        // gather payloads first (the job may sit in the caller's arrays)
-        V gv[VB ? ITEMS : 1];
         if (VB) {
+            // gather payloads before any write (the job may sit in the caller's arrays)
+            V gv[VB ? ITEMS : 1];
 #pragma unroll
             for (int r = 0; r < ITEMS; r++) {
                 const int i = r * kThreads + tid;
-                if (i < len) gv[VB ? r : 0] = vsrc[s.idx[i]];
+                if (r < iu && i < len) gv[VB ? r : 0] = vsrc[min((int)s.perm[i], len - 1)];
             }
-        }
-        __syncthreads();
+            __syncthreads();
 #pragma unroll
-        for (int r = 0; r < ITEMS; r++) {
-            const int i = r * kThreads + tid;
-            if (i < len) {
-                dst[i] = skeys[i];
-                if (VB) vdst[i] = gv[VB ? r : 0];
+            for (int r = 0; r < ITEMS; r++) {
+                const int i = r * kThreads + tid;
+                if (r < iu && i < len) {
+                    dst[i] = skeys[min((int)s.perm[i], len - 1)];
+                    vdst[i] = gv[VB ? r : 0];
+                }
             }
+        } else {
+            for (int i = tid; i < len; i += kThreads) dst[i] = skeys[min((int)s.perm[i], len - 1)];
         }
         __syncthreads();
     }
