@@ -122,6 +122,11 @@ template <> struct KeyTraits<4> {
     __device__ static __forceinline__ uint32_t digit(Bits b, int pos) {
         return (b << pos) >> (32 - kBits);       // pos < 32
     }
+    // nb (< 32) bits starting at bit position pos (0 = MSB); bits past the key read as 0
+    __device__ static __forceinline__ uint32_t bits_at(Bits b, int pos, int nb) {
+        return (b << pos) >> (32 - nb);
+    }
+    __device__ static __forceinline__ bool less(Bits a, Bits b) { return a < b; }
     __device__ static __forceinline__ Bits ones() { return 0xffffffffu; }
     __device__ static __forceinline__ Bits zero() { return 0u; }
     // first bit position (0 = MSB) where a and o differ, or kW if equal
@@ -152,6 +157,10 @@ template <> struct KeyTraits<8> {
     __device__ static __forceinline__ uint32_t digit(Bits b, int pos) {
         return (uint32_t)((b << pos) >> (64 - kBits));   // pos < 64
     }
+    __device__ static __forceinline__ uint32_t bits_at(Bits b, int pos, int nb) {
+        return (uint32_t)((b << pos) >> (64 - nb));
+    }
+    __device__ static __forceinline__ bool less(Bits a, Bits b) { return a < b; }
     __device__ static __forceinline__ Bits ones() { return ~0ull; }
     __device__ static __forceinline__ Bits zero() { return 0ull; }
     __device__ static __forceinline__ int first_diff(Bits a, Bits o) {
@@ -185,6 +194,15 @@ template <> struct KeyTraits<16> {
         else top = b.lo << (pos - 64);
         return (uint32_t)(top >> (64 - kBits));
     }
+    __device__ static __forceinline__ uint32_t bits_at(Bits b, int pos, int nb) {
+        uint64_t top;
+        if (pos < 64) top = pos ? ((b.hi << pos) | (b.lo >> (64 - pos))) : b.hi;
+        else top = b.lo << (pos - 64);
+        return (uint32_t)(top >> (64 - nb));
+    }
+    __device__ static __forceinline__ bool less(Bits a, Bits b) {
+        return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+    }
     __device__ static __forceinline__ Bits ones() { return Bits{~0ull, ~0ull}; }
     __device__ static __forceinline__ Bits zero() { return Bits{0ull, 0ull}; }
     __device__ static __forceinline__ int first_diff(Bits a, Bits o) {
@@ -200,6 +218,40 @@ template <> struct KeyTraits<16> {
     __device__ static __forceinline__ Bits unpack(uint4 v) {
         return Bits{((uint64_t)v.w << 32) | v.z, ((uint64_t)v.y << 32) | v.x};
     }
+};
+
+// Branch-free key encoders: built once per kernel from the runtime map, so the
+// per-key encoding is a byte swap (selected) and one XOR with a mask.
+template <int KB> struct Encoder;
+
+template <> struct Encoder<4> {
+    bool bswap;
+    uint32_t fmask, smask;
+    __device__ explicit Encoder(int map)
+        : bswap(map == BINAR_MAP_BYTES_BE), fmask(map == BINAR_MAP_FLOAT ? ~0u : 0u),
+          smask((map == BINAR_MAP_SIGNED || map == BINAR_MAP_FLOAT) ? 0x80000000u : 0u) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+        if (bswap) x = __byte_perm(x, 0, 0x0123);
+        return x ^ (((uint32_t)((int32_t)x >> 31) & fmask) | smask);
+    }
+};
+
+template <> struct Encoder<8> {
+    bool bswap;
+    uint64_t fmask, smask;
+    __device__ explicit Encoder(int map)
+        : bswap(map == BINAR_MAP_BYTES_BE), fmask(map == BINAR_MAP_FLOAT ? ~0ull : 0ull),
+          smask((map == BINAR_MAP_SIGNED || map == BINAR_MAP_FLOAT) ? 0x8000000000000000ull : 0ull) {}
+    __device__ __forceinline__ uint64_t operator()(uint64_t x) const {
+        if (bswap) x = KeyTraits<8>::bswap64(x);
+        return x ^ (((uint64_t)((int64_t)x >> 63) & fmask) | smask);
+    }
+};
+
+template <> struct Encoder<16> {
+    int map;
+    __device__ explicit Encoder(int m) : map(m) {}
+    __device__ __forceinline__ U128 operator()(uint4 x) const { return KeyTraits<16>::encode(x, map); }
 };
 
 __device__ __forceinline__ U128 operator&(U128 a, U128 b) { return U128{a.hi & b.hi, a.lo & b.lo}; }

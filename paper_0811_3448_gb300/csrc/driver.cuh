@@ -109,7 +109,7 @@ int run_call_vb(const Call &c) {
     }
     {
         auto ffn = k_finish<KB, VB>;
-        const size_t smem = sizeof(FinishSmem<KB>);
+        const size_t smem = sizeof(FinishSmem<KB, VB>);
         const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
         if ((rc = launch("finish", -1, c.stream, [&] {
                  ffn<<<sms * (occ > 0 ? occ : 1), kThreads, smem, c.stream>>>(ws, p, k0, k1, v0, v1);

@@ -388,6 +388,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
     __shared__ uint4 sand[kWarps], sor[kWarps];
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
+    const Encoder<KB> enc(p.map);
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
         const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
         Bits a = KT::ones(), o = KT::zero();
         for (int i = tid; i < tlen; i += kThreads) {
-            const Bits x = KT::encode(src[i], p.map);
+            const Bits x = enc(src[i]);
             a = a & x;
             o = o | x;
             const uint32_t d = KT::digit(x, bk.pos);
@@ -697,6 +698,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
+    const Encoder<KB> enc(p.map);
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     const uint32_t *prefix = slot ? ws.hist[1] : ws.hist[0];
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
@@ -731,7 +733,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             const int i = striped(ITEMS, j);
-            pk.set_dig(j, i < tlen ? KT::digit(KT::encode(skeys[i], p.map), bk.pos) : 0u);
+            pk.set_dig(j, i < tlen ? KT::digit(enc(skeys[i]), bk.pos) : 0u);
         }
         rank_tile<ITEMS>(pk, ITEMS, tlen, s.rank);
 
@@ -790,7 +792,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     q = 0;
                 }
                 const Raw k = skeys[q];
-                const uint32_t d = KT::digit(KT::encode(k, p.map), bk.pos);
+                const uint32_t d = KT::digit(enc(k), bk.pos);
                 const long long at = s.offs[d] + i;
                 if (at >= bk.begin && at < bend) {
                     dst[at] = k;
@@ -806,27 +808,47 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // ---------------------------------------------------------------------------
 // finish: one small bucket (job) per ticket, sorted inside shared memory on
-// bits pos .. w-1 by an LSD radix sort over 8-bit windows (the last window
-// starts at pos and may overlap the one below it); windows whose bits are
-// equal across the bucket are skipped.  The keys stay where cp.async put them;
-// each window pass refines a permutation perm[sorted position] = input
-// position.  Every pass is stable except the first one of a key-only sort.
-// Keys are written to the caller's key array, payloads gathered from the
-// job's buffer through the permutation.  Items per thread follow the job size
-// (iu = ceil(len / 256)).
+// bits pos .. w-1 -- the rest of the recursion for that sub-array.  Keys and
+// payloads are staged in shared memory with cp.async.
+//
+// Fast path: bits above the first bit f where the job's keys differ are equal
+// (AND / OR of the encoded keys), so one MSD split on the 11 bits at f leaves
+// runs of about len / 2048 keys.  The split uses one shared-memory atomic per
+// key (unstable); then every key counts the keys of its run that precede it in
+// (encoded key, input position) order -- the stable order -- and is written
+// straight to its final place.  If a run holds more than kFinishRun keys
+// (heavy duplication) the job falls back to an LSD radix sort over 8-bit
+// windows with stable passes (the last window starts at pos; windows whose
+// bits are equal across the job are skipped; the first pass of a key-only
+// sort may be unstable), which builds perm[sorted position] = input position.
 // ---------------------------------------------------------------------------
-template <int KB>
+constexpr int kFinishBits = 11;
+constexpr int kFinishBins = 1 << kFinishBits;
+constexpr int kFinishRun = 32;
+
+struct FinishFastSmem {
+    uint32_t cnt[kFinishBins];
+    uint32_t start[kFinishBins];
+    uint32_t scratch[kWarps];
+    uint32_t maxrun;
+};
+
+template <int KB, int VB>
 struct FinishSmem {
     static constexpr int T = TileShape<KB>::kTile;
-    RankSmem rank;
+    union {
+        RankSmem rank;
+        FinishFastSmem fast;
+    } u;
     uint4 sand[kWarps], sor[kWarps];
     uint32_t ticket;
     alignas(16) unsigned char keys[T * KB];
+    alignas(16) unsigned char vals[VB ? T * VB : 16];
     uint16_t perm[T];
 };
 
 template <int KB, int VB>
-__global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
+__global__ void __launch_bounds__(kThreads, VB == 0 ? 3 : 2)
     k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
@@ -835,9 +857,11 @@ __global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
     constexpr int ITEMS = TileShape<KB>::kItems;
     constexpr int W = KT::kW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &s = *reinterpret_cast<FinishSmem<KB> *>(smem_raw);
+    auto &s = *reinterpret_cast<FinishSmem<KB, VB> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
+    V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
+    const Encoder<KB> enc(p.map);
     const uint32_t njobs = min(ws.ctr->njobs, ws.jcap);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (;;) {
@@ -861,13 +885,15 @@ __global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
             }
             continue;
         }
-        for (int i = tid; i < len; i += kThreads) cp_async<KB>(&skeys[i], &src[i]);
+        for (int i = tid; i < len; i += kThreads) {
+            cp_async<KB>(&skeys[i], &src[i]);
+            if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
+        }
         cp_async_wait_all();
         __syncthreads();
-        const int iu = (len + kThreads - 1) / kThreads;
         Bits a = KT::ones(), o = KT::zero();
         for (int i = tid; i < len; i += kThreads) {
-            const Bits x = KT::encode(skeys[i], p.map);
+            const Bits x = enc(skeys[i]);
             a = a & x;
             o = o | x;
         }
@@ -887,6 +913,9 @@ __global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
             s.sand[w] = pa;
             s.sor[w] = po;
         }
+        FinishFastSmem &fs = s.u.fast;
+        for (int i = tid; i < kFinishBins; i += kThreads) fs.cnt[i] = 0;
+        if (tid == 0) fs.maxrun = 0;
         __syncthreads();
         uint4 ra = s.sand[0], ro = s.sor[0];
         for (int i = 1; i < kWarps; i++) {
@@ -894,79 +923,142 @@ __global__ void __launch_bounds__(kThreads, VB == 8 ? 2 : 3)
             ro.x |= s.sor[i].x; ro.y |= s.sor[i].y; ro.z |= s.sor[i].z; ro.w |= s.sor[i].w;
         }
         const Bits diff_a = KT::unpack(ra), diff_o = KT::unpack(ro);
-        // LSD over windows [q, q+8): q = w-8, w-16, ... while q > pos, then q = pos
-        int q = W - kBits;
-        bool moved = false;
-        Packed<ITEMS> pk;
-        uint32_t src_pos[(ITEMS + 1) / 2];   // input positions of this thread's items, packed
-        for (;;) {
-            const int qq = q > (int)job.pos ? q : (int)job.pos;
-            const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
-            if (varies) {
-                if (moved) __syncthreads();
-#pragma unroll
-                for (int j = 0; j < ITEMS; j++) {
-                    if (j < iu) {
-                        const int i = striped(iu, j);
-                        uint32_t x = 0;
-                        if (i < len) x = moved ? s.perm[i] : (uint32_t)i;
-                        if (x >= (uint32_t)len) {
-                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                            x = 0;
-                        }
-                        if ((j & 1) == 0) src_pos[j >> 1] = x;
-                        else src_pos[j >> 1] |= x << 16;
-                        pk.set_dig(j, i < len ? KT::digit(KT::encode(skeys[x], p.map), qq) : 0u);
-                    }
-                }
-                if (VB || moved) rank_stable<ITEMS>(pk, iu, len, s.rank);
-                else rank_unstable<ITEMS>(pk, iu, len, s.rank);
-#pragma unroll
-                for (int j = 0; j < ITEMS; j++) {
-                    if (j < iu && striped(iu, j) < len) {
-                        const uint32_t r = pk.rank(j);
-                        if (r < (uint32_t)len)
-                            s.perm[r] = (uint16_t)(src_pos[j >> 1] >> ((j & 1) * 16));
-                        else
-                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                    }
-                }
-                moved = true;
-            }
-            if (qq == (int)job.pos) break;
-            q -= kBits;
-        }
-        __syncthreads();
-        if (!moved) {
-            // already in order: only a move from the workspace, if any
+        const int f = KT::first_diff(diff_a, diff_o);
+        if (f >= W) {
+            // all keys equal: already in order
             if (job.buf == 1) {
                 for (int i = tid; i < len; i += kThreads) {
                     dst[i] = skeys[i];
-                    if (VB) vdst[i] = vsrc[i];
+                    if (VB) vdst[i] = svals[i];
                 }
             }
             __syncthreads();
             continue;
         }
-        if (VB) {
-            // gather payloads before any write (the job may sit in the caller's arrays)
-            V gv[VB ? ITEMS : 1];
+
+        // ---- fast path: unstable 11-bit split at f ----
+        uint32_t dr[ITEMS];   // (digit << 16) | rank within the digit
 #pragma unroll
-            for (int r = 0; r < ITEMS; r++) {
-                const int i = r * kThreads + tid;
-                if (r < iu && i < len) gv[VB ? r : 0] = vsrc[min((int)s.perm[i], len - 1)];
+        for (int k = 0; k < ITEMS; k++) {
+            if (k * kThreads < len) {
+                const int i = k * kThreads + tid;
+                const bool valid = i < len;
+                const uint32_t d = valid ? KT::bits_at(enc(skeys[i]), f, kFinishBits) : 0u;
+                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+                uint32_t r = 0;
+                if (__all_sync(0xffffffffu, valid && d == d0)) {
+                    uint32_t c = 0;
+                    if (lane == 0) c = atomicAdd(&fs.cnt[d0], 32u);
+                    r = __shfl_sync(0xffffffffu, c, 0) + lane;
+                } else if (valid) {
+                    r = atomicAdd(&fs.cnt[d], 1u);
+                }
+                dr[k] = (d << 16) | r;
+            }
+        }
+        __syncthreads();
+        {
+            constexpr int PER = kFinishBins / kThreads;
+            uint32_t c[PER], sum = 0, mx = 0;
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                c[q] = fs.cnt[tid * PER + q];
+                sum += c[q];
+                mx = max(mx, c[q]);
+            }
+            uint32_t total;
+            uint32_t run = block_exclusive_scan(sum, fs.scratch, &total);
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                fs.start[tid * PER + q] = run;
+                run += c[q];
+            }
+            if (mx > kFinishRun) atomicMax(&fs.maxrun, mx);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++) {
+            const int i = k * kThreads + tid;
+            if (k * kThreads < len && i < len) {
+                const uint32_t at = fs.start[dr[k] >> 16] + (dr[k] & 0xffffu);
+                if (at < (uint32_t)len) s.perm[at] = (uint16_t)i;
+                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+            }
+        }
+        __syncthreads();
+        if (fs.maxrun <= (uint32_t)kFinishRun) {
+            // every key's place in its run: the run's keys that precede it in
+            // (encoded key, input position) order; written straight to the output
+#pragma unroll 4
+            for (int x = tid; x < len; x += kThreads) {
+                const uint32_t i = s.perm[x];
+                const Bits ki = enc(skeys[i]);
+                const uint32_t d = KT::bits_at(ki, f, kFinishBits);
+                const int b0 = (int)fs.start[d], m = (int)fs.cnt[d];
+                int rank = 0;
+                for (int y = b0; y < b0 + m; y++) {
+                    const uint32_t j = s.perm[y];
+                    const Bits kj = enc(skeys[j]);
+                    rank += (KT::less(kj, ki) || (!KT::less(ki, kj) && j < i)) ? 1 : 0;
+                }
+                const int at = min(b0 + rank, len - 1);
+                dst[at] = skeys[i];
+                if (VB) vdst[at] = svals[i];
             }
             __syncthreads();
+            continue;
+        }
+
+        // ---- fallback: stable LSD over 8-bit windows, from the input order ----
+        {
+            const int iu = (len + kThreads - 1) / kThreads;
+            int q = W - kBits;
+            bool moved = false;
+            Packed<ITEMS> pk;
+            uint32_t src_pos[(ITEMS + 1) / 2];
+            for (;;) {
+                const int qq = q > (int)job.pos ? q : (int)job.pos;
+                const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
+                if (varies) {
+                    __syncthreads();
 #pragma unroll
-            for (int r = 0; r < ITEMS; r++) {
-                const int i = r * kThreads + tid;
-                if (r < iu && i < len) {
-                    dst[i] = skeys[min((int)s.perm[i], len - 1)];
-                    vdst[i] = gv[VB ? r : 0];
+                    for (int j = 0; j < ITEMS; j++) {
+                        if (j < iu) {
+                            const int i = striped(iu, j);
+                            uint32_t x = 0;
+                            if (i < len) x = moved ? s.perm[i] : (uint32_t)i;
+                            if (x >= (uint32_t)len) {
+                                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                                x = 0;
+                            }
+                            if ((j & 1) == 0) src_pos[j >> 1] = x;
+                            else src_pos[j >> 1] |= x << 16;
+                            pk.set_dig(j, i < len ? KT::digit(enc(skeys[x]), qq) : 0u);
+                        }
+                    }
+                    if (VB || moved) rank_stable<ITEMS>(pk, iu, len, s.u.rank);
+                    else rank_unstable<ITEMS>(pk, iu, len, s.u.rank);
+#pragma unroll
+                    for (int j = 0; j < ITEMS; j++) {
+                        if (j < iu && striped(iu, j) < len) {
+                            const uint32_t r = pk.rank(j);
+                            if (r < (uint32_t)len)
+                                s.perm[r] = (uint16_t)(src_pos[j >> 1] >> ((j & 1) * 16));
+                            else
+                                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                        }
+                    }
+                    moved = true;
                 }
+                if (qq == (int)job.pos) break;
+                q -= kBits;
             }
-        } else {
-            for (int i = tid; i < len; i += kThreads) dst[i] = skeys[min((int)s.perm[i], len - 1)];
+        }
+        __syncthreads();
+        for (int x = tid; x < len; x += kThreads) {
+            const int i = min((int)s.perm[x], len - 1);
+            dst[x] = skeys[i];
+            if (VB) vdst[x] = svals[i];
         }
         __syncthreads();
     }
