@@ -105,7 +105,8 @@ int check_types(int key_bytes, int map, int val_bytes) {
 // Resolves a (nullable) config for the key size into the call.
 int resolve_config(const binar_config *cfg, int key_bytes, Call &c) {
     const int T = tile_for(key_bytes);
-    c.cutoff = T;
+    const int cap = finish_cap_for(key_bytes);
+    c.cutoff = cap;
     c.ctas_per_sm = 0;
     c.timeout_ns = 1000000000LL;
     c.skip_publish_tile = -1;
@@ -113,7 +114,7 @@ int resolve_config(const binar_config *cfg, int key_bytes, Call &c) {
     if (cfg->tile_keys != 0 && cfg->tile_keys != T) return BINAR_ERR_UNSUPPORTED;
     if (cfg->bits_per_pass != 0 && cfg->bits_per_pass != kBits) return BINAR_ERR_UNSUPPORTED;
     if (cfg->small_cutoff != 0) {
-        if (cfg->small_cutoff < kMinCutoff || cfg->small_cutoff > T) return BINAR_ERR_INVALID_ARG;
+        if (cfg->small_cutoff < kMinCutoff || cfg->small_cutoff > cap) return BINAR_ERR_INVALID_ARG;
         c.cutoff = cfg->small_cutoff;
     }
     if (cfg->ctas_per_sm < 0 || cfg->lookback_timeout_ns < 0) return BINAR_ERR_INVALID_ARG;

@@ -58,6 +58,8 @@ struct CopyJob {
 };
 static_assert(sizeof(CopyJob) == 16, "CopyJob layout");
 
+constexpr int kMaxClasses = 8;          // finisher size classes
+
 struct Counters {
     uint32_t status;                  // first device error (binar_status), 0 = OK
     uint32_t njobs;                   // finisher jobs
@@ -65,9 +67,14 @@ struct Counters {
     unsigned long long copy_alloc;    // (tiles << 32) | copy jobs
     uint32_t ticket_hist, ticket_part, ticket_fin, ticket_copy;
     uint32_t ticket_prep;
-    uint32_t pad[7];
+    uint32_t njobs2;                  // finisher jobs left to the LSD path
+    uint32_t ticket_fin2;
+    uint32_t pad[5];
+    uint32_t class_count[kMaxClasses];   // finisher jobs per size class
+    uint32_t class_cursor[kMaxClasses];  // binning cursors
+    uint32_t class_ticket[kMaxClasses];  // per-class work tickets
 };
-static_assert(sizeof(Counters) == 80, "Counters layout");
+static_assert(sizeof(Counters) == 176, "Counters layout");
 
 // Device view of the caller's workspace, carved by the host driver.
 struct Ws {
@@ -80,6 +87,8 @@ struct Ws {
     uint32_t *tilemap;             // [tile] -> bucket index in the current list
     uint32_t *cells;               // [tile][kRadix] look-back cells
     Job *jobs;
+    uint32_t *jobidx;              // job indices grouped by size class
+    Job *jobs2;                    // jobs the finisher's fast path hands to the LSD path
     CopyJob *copies;
     uint32_t mcap, tcap, jcap, ccap;   // capacities: buckets, tiles, jobs, copy jobs
 };
@@ -252,6 +261,54 @@ template <> struct Encoder<16> {
     int map;
     __device__ explicit Encoder(int m) : map(m) {}
     __device__ __forceinline__ U128 operator()(uint4 x) const { return KeyTraits<16>::encode(x, map); }
+};
+
+// Inverses of the encoders (encoded bit string -> raw key).
+template <int KB> struct Decoder;
+
+template <> struct Decoder<4> {
+    bool bswap;
+    uint32_t fmask, smask;
+    __device__ explicit Decoder(int map)
+        : bswap(map == BINAR_MAP_BYTES_BE), fmask(map == BINAR_MAP_FLOAT ? ~0u : 0u),
+          smask((map == BINAR_MAP_SIGNED || map == BINAR_MAP_FLOAT) ? 0x80000000u : 0u) {}
+    __device__ __forceinline__ uint32_t operator()(uint32_t e) const {
+        uint32_t x = e ^ (((uint32_t)((int32_t)~e >> 31) & fmask) | smask);
+        return bswap ? __byte_perm(x, 0, 0x0123) : x;
+    }
+};
+
+template <> struct Decoder<8> {
+    bool bswap;
+    uint64_t fmask, smask;
+    __device__ explicit Decoder(int map)
+        : bswap(map == BINAR_MAP_BYTES_BE), fmask(map == BINAR_MAP_FLOAT ? ~0ull : 0ull),
+          smask((map == BINAR_MAP_SIGNED || map == BINAR_MAP_FLOAT) ? 0x8000000000000000ull : 0ull) {}
+    __device__ __forceinline__ uint64_t operator()(uint64_t e) const {
+        uint64_t x = e ^ (((uint64_t)((int64_t)~e >> 63) & fmask) | smask);
+        return bswap ? KeyTraits<8>::bswap64(x) : x;
+    }
+};
+
+template <> struct Decoder<16> {
+    int map;
+    __device__ explicit Decoder(int m) : map(m) {}
+    __device__ __forceinline__ uint4 operator()(U128 e) const {
+        uint4 x;
+        if (map == BINAR_MAP_BYTES_BE) {
+            x.x = __byte_perm((uint32_t)(e.hi >> 32), 0, 0x0123);
+            x.y = __byte_perm((uint32_t)e.hi, 0, 0x0123);
+            x.z = __byte_perm((uint32_t)(e.lo >> 32), 0, 0x0123);
+            x.w = __byte_perm((uint32_t)e.lo, 0, 0x0123);
+        } else {
+            const uint64_t hi = map == BINAR_MAP_SIGNED ? e.hi ^ 0x8000000000000000ull : e.hi;
+            x.x = (uint32_t)e.lo;
+            x.y = (uint32_t)(e.lo >> 32);
+            x.z = (uint32_t)hi;
+            x.w = (uint32_t)(hi >> 32);
+        }
+        return x;
+    }
 };
 
 __device__ __forceinline__ U128 operator&(U128 a, U128 b) { return U128{a.hi & b.hi, a.lo & b.lo}; }

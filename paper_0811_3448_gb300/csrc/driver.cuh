@@ -5,6 +5,8 @@
 // caller's stream; nothing allocates or synchronises.
 #pragma once
 
+#include <utility>
+
 #include "kernels.cuh"
 #include "layout.cuh"
 
@@ -23,9 +25,29 @@ int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int
     });
 }
 
+template <int KB, int VB, int CLS>
+int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1, void *v0,
+                        void *v1) {
+    constexpr int IU = FinishClasses<KB>::iu(CLS);
+    auto ffn = k_finish<KB, VB, CLS>;
+    const size_t smem = sizeof(FinishSmem<KB, VB, IU>);
+    const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
+    return launch("finish", CLS, c.stream, [&] {
+        ffn<<<device_sms() * (occ > 0 ? occ : 1), kThreads, smem, c.stream>>>(ws, p, k0, k1, v0, v1);
+    });
+}
+
+template <int KB, int VB, int... CLS>
+int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1,
+                          void *v0, void *v1, std::integer_sequence<int, CLS...>) {
+    int rc = BINAR_OK;
+    ((rc = rc ? rc : launch_finish_class<KB, VB, CLS>(c, ws, p, k0, k1, v0, v1)), ...);
+    return rc;
+}
+
 template <int KB, int VB>
 int run_call_vb(const Call &c) {
-    constexpr int T = TileShape<KB>::kTile;
+    constexpr int T = PartShape<KB>::kTile;
     constexpr int STABLE = VB > 0;
     const int L = levels_for(KB);
     const int sms = device_sms();
@@ -46,7 +68,7 @@ int run_call_vb(const Call &c) {
         p.vals = const_cast<void *>(c.vals_in);
         const uint32_t tiles = (uint32_t)((c.n + T - 1) / T);
         if ((rc = launch("init", -1, c.stream, [&] {
-                 k_init<<<1, 1, 0, c.stream>>>(ws, c.n, 0, c.pass_pos, tiles, 1);
+                 k_init<KB><<<1, 1, 0, c.stream>>>(ws, c.n, 0, c.pass_pos, tiles, 1);
              })))
             return rc;
         if ((rc = launch("prep", 0, c.stream, [&] { k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, 0); })))
@@ -73,7 +95,7 @@ int run_call_vb(const Call &c) {
     const bool seg = c.offsets != nullptr;
     const uint32_t tiles0 = (uint32_t)((c.n + T - 1) / T);
     if ((rc = launch("init", -1, c.stream, [&] {
-             k_init<<<1, 1, 0, c.stream>>>(ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
+             k_init<KB><<<1, 1, 0, c.stream>>>(ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
          })))
         return rc;
     if (seg) {
@@ -82,7 +104,7 @@ int run_call_vb(const Call &c) {
         if (grid > small_grid) grid = small_grid;
         if (grid < 1) grid = 1;
         if ((rc = launch("seed", -1, c.stream, [&] {
-                 k_seed_segments<<<grid, kThreads, 0, c.stream>>>(ws, c.offsets, S, c.n, c.cutoff, T);
+                 k_seed_segments<KB><<<grid, kThreads, 0, c.stream>>>(ws, c.offsets, S, c.n, c.cutoff, T);
              })))
             return rc;
     }
@@ -108,11 +130,18 @@ int run_call_vb(const Call &c) {
         }
     }
     {
-        auto ffn = k_finish<KB, VB>;
-        const size_t smem = sizeof(FinishSmem<KB, VB>);
-        const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
-        if ((rc = launch("finish", -1, c.stream, [&] {
-                 ffn<<<sms * (occ > 0 ? occ : 1), kThreads, smem, c.stream>>>(ws, p, k0, k1, v0, v1);
+        if ((rc = launch("bin_jobs", -1, c.stream, [&] {
+                 k_bin_jobs<KB><<<small_grid, kThreads, 0, c.stream>>>(ws);
+             })))
+            return rc;
+        if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k1, v0, v1,
+                                                 std::make_integer_sequence<int, FinishClasses<KB>::kCount>{})))
+            return rc;
+        auto lfn = k_finish_lsd<KB, VB>;
+        const size_t lsmem = sizeof(FinishLsdSmem<KB, VB>);
+        const int locc = kernel_ctas_per_sm((const void *)lfn, lsmem);
+        if ((rc = launch("finish_lsd", -1, c.stream, [&] {
+                 lfn<<<sms * (locc > 0 ? locc : 1), kThreads, lsmem, c.stream>>>(ws, p, k0, k1, v0, v1);
              })))
             return rc;
     }

@@ -20,9 +20,14 @@
 
 namespace binar {
 
-// Items per thread of a tile, by key size: 8192 / 4096 / 2048 keys per tile.
+// Items per thread of the finisher's largest job: 8192 / 4096 / 2048 keys.
 template <int KB> struct TileShape {
     static constexpr int kItems = KB == 4 ? 32 : (KB == 8 ? 16 : 8);
+    static constexpr int kTile = kThreads * kItems;
+};
+// Items per thread of a partition / histogram tile: 4096 / 2048 / 2048 keys.
+template <int KB> struct PartShape {
+    static constexpr int kItems = KB == 4 ? 16 : 8;
     static constexpr int kTile = kThreads * kItems;
 };
 
@@ -251,18 +256,56 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 // ---------------------------------------------------------------------------
+// Finisher size classes: a job of len keys is finished by the kernel whose
+// capacity kThreads * IU is the smallest that holds it, so that every class
+// kernel unrolls its loops with known bounds and sizes its shared memory and
+// registers to its class.
+// ---------------------------------------------------------------------------
+template <int KB> struct FinishClasses;
+template <> struct FinishClasses<4> {
+    static constexpr int kCount = 6;
+    __host__ __device__ static constexpr int iu(int c) {
+        return c == 0 ? 4 : c == 1 ? 8 : c == 2 ? 12 : c == 3 ? 18 : c == 4 ? 24 : 32;
+    }
+};
+template <> struct FinishClasses<8> {
+    static constexpr int kCount = 4;
+    __host__ __device__ static constexpr int iu(int c) { return c == 0 ? 4 : c == 1 ? 8 : c == 2 ? 12 : 16; }
+};
+template <> struct FinishClasses<16> {
+    static constexpr int kCount = 2;
+    __host__ __device__ static constexpr int iu(int c) { return c == 0 ? 4 : 8; }
+};
+
+template <int KB>
+__device__ __forceinline__ int finish_class(uint32_t len) {
+    int c = 0;
+    while (c + 1 < FinishClasses<KB>::kCount && (uint32_t)(kThreads * FinishClasses<KB>::iu(c)) < len) c++;
+    return c;
+}
+
+// Appends a finisher job and counts it in its size class.
+template <int KB>
+__device__ __forceinline__ void push_job(const Ws &ws, const Job &j) {
+    const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
+    if (ji >= ws.jcap) {
+        set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+        return;
+    }
+    ws.jobs[ji] = j;
+    atomicAdd(&ws.ctr->class_count[finish_class<KB>(j.len)], 1u);
+}
+
+// ---------------------------------------------------------------------------
 // init: resets the counters and seeds level 0 with the whole array, or the
 // finisher with it when it is small.  One thread.
 // ---------------------------------------------------------------------------
-static __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0, int seed_list) {
+template <int KB>
+__global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0, int seed_list) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Counters *c = ws.ctr;
-    c->status = 0;
-    c->njobs = 0;
-    c->alloc[0] = 0;
-    c->alloc[1] = 0;
-    c->copy_alloc = 0;
-    c->ticket_hist = c->ticket_part = c->ticket_fin = c->ticket_copy = c->ticket_prep = 0;
+    uint32_t *cw = reinterpret_cast<uint32_t *>(c);
+    for (int i = 0; i < (int)(sizeof(Counters) / 4); i++) cw[i] = 0;
     if (!seed_list) return;
     if (n > cutoff) {
         Bucket b;
@@ -282,15 +325,15 @@ static __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t
         j.pos = (uint16_t)pos0;
         j.buf = 0;
         j.pad = 0;
-        ws.jobs[0] = j;
-        c->njobs = 1;
+        push_job<KB>(ws, j);
     }
 }
 
 // seed_segments: segment s = [offsets[s], offsets[s+1]) becomes a level-0
 // bucket (more than `cutoff` keys), a finisher job (2..cutoff keys) or
 // nothing (0 or 1 key).
-static __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_segments,
+template <int KB>
+__global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_segments,
                                 long long n, int cutoff, int tile) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < num_segments;
@@ -320,18 +363,13 @@ static __global__ void k_seed_segments(Ws ws, const long long *offsets, long lon
             bk.pad = 0;
             ws.list[0][bi] = bk;
         } else if (len >= 2) {
-            const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
-            if (ji >= ws.jcap) {
-                set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
-                continue;
-            }
             Job j;
             j.begin = a;
             j.len = (uint32_t)len;
             j.pos = 0;
             j.buf = 0;
             j.pad = 0;
-            ws.jobs[ji] = j;
+            push_job<KB>(ws, j);
         }
     }
 }
@@ -383,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
-    constexpr int T = TileShape<KB>::kTile;
+    constexpr int T = PartShape<KB>::kTile;
     __shared__ uint32_t sh[kRadix];
     __shared__ uint4 sand[kWarps], sor[kWarps];
     __shared__ uint32_t sticket;
@@ -469,7 +507,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     using KT = KeyTraits<KB>;
     using Bits = typename KT::Bits;
     constexpr int W = KT::kW;
-    constexpr int T = TileShape<KB>::kTile;
+    constexpr int T = PartShape<KB>::kTile;
     __shared__ uint32_t scount[kRadix];
     __shared__ uint32_t sexcl[kRadix];
     __shared__ uint32_t scratch[kWarps];
@@ -576,18 +614,13 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 int jpos = terminal ? W : (children == 1 ? cpos : bk.pos);
                 if (terminal && cbuf == 0) return;          // finished in place
                 if (!terminal && len == 1 && cbuf == 0) return;
-                const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
-                if (ji >= ws.jcap) {
-                    set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
-                    return;
-                }
                 Job j;
                 j.begin = begin;
                 j.len = len;
                 j.pos = (uint16_t)jpos;
                 j.buf = (uint8_t)cbuf;
                 j.pad = 0;
-                ws.jobs[ji] = j;
+                push_job<KB>(ws, j);
             };
             (void)run_child_pos;
             for (int d = 0; d < kRadix; d++) {
@@ -675,24 +708,24 @@ constexpr uint32_t kInclusive = 0x80000000u;
 
 template <int KB, int VB, bool STABLE>
 struct PartitionSmem {
-    static constexpr int T = TileShape<KB>::kTile;
+    static constexpr int T = PartShape<KB>::kTile;
     typename RankSmemFor<STABLE>::T rank;
     long long offs[kRadix];
-    uint32_t ticket;
+    uint32_t next_ticket;
     alignas(16) unsigned char keys[T * KB];
     alignas(16) unsigned char vals[VB ? T * VB : 16];
     uint16_t perm[T];
 };
 
 template <int KB, int VB, bool STABLE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
     k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
                 void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int ITEMS = TileShape<KB>::kItems;
-    constexpr int T = TileShape<KB>::kTile;
+    constexpr int ITEMS = PartShape<KB>::kItems;
+    constexpr int T = PartShape<KB>::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
@@ -705,9 +738,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const int tid = threadIdx.x;
     for (;;) {
-        if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
+        if (tid == 0) s.next_ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
         __syncthreads();
-        const uint32_t t = s.ticket;
+        const uint32_t t = s.next_ticket;
         __syncthreads();
         if (t >= nt) break;
         const uint32_t b = ws.tilemap[t];
@@ -812,34 +845,321 @@ __global__ void __launch_bounds__(kThreads, 2)
 // payloads are staged in shared memory with cp.async.
 //
 // Fast path: bits above the first bit f where the job's keys differ are equal
-// (AND / OR of the encoded keys), so one MSD split on the 11 bits at f leaves
-// runs of about len / 2048 keys.  The split uses one shared-memory atomic per
-// key (unstable); then every key counts the keys of its run that precede it in
-// (encoded key, input position) order -- the stable order -- and is written
-// straight to its final place.  If a run holds more than kFinishRun keys
+// (AND / OR of the encoded keys), so one MSD split on the 12 bits at f leaves
+// runs of about len / 4096 keys.  The split uses one shared-memory atomic per
+// key (unstable); the encoded keys are placed in split order, then every key
+// counts the keys of its run that precede it in (encoded key, input position)
+// order -- the stable order -- and is written straight to its final place.  If a run holds more than kFinishRun keys
 // (heavy duplication) the job falls back to an LSD radix sort over 8-bit
 // windows with stable passes (the last window starts at pos; windows whose
 // bits are equal across the job are skipped; the first pass of a key-only
 // sort may be unstable), which builds perm[sorted position] = input position.
 // ---------------------------------------------------------------------------
-constexpr int kFinishBits = 11;
+constexpr int kFinishBits = 12;
 constexpr int kFinishBins = 1 << kFinishBits;
 constexpr int kFinishRun = 32;
 
+// 16-bit counters and run starts, two per word (counts and starts stay below
+// the job size, < 65536).
 struct FinishFastSmem {
-    uint32_t cnt[kFinishBins];
-    uint32_t start[kFinishBins];
+    uint32_t cnt2[kFinishBins / 2];
+    uint32_t start2[kFinishBins / 2];
     uint32_t scratch[kWarps];
     uint32_t maxrun;
 };
+__device__ __forceinline__ uint32_t half16(const uint32_t *a, uint32_t d) {
+    return (a[d >> 1] >> ((d & 1) * 16)) & 0xffffu;
+}
 
-template <int KB, int VB>
+template <int KB, int VB, int IU>
 struct FinishSmem {
-    static constexpr int T = TileShape<KB>::kTile;
+    static constexpr int T = kThreads * IU;
     union {
-        RankSmem rank;
         FinishFastSmem fast;
     } u;
+    uint4 sand[kWarps], sor[kWarps];
+    uint32_t next_ticket;
+    Job next_job;
+    alignas(16) unsigned char keys[T * KB];
+    alignas(16) unsigned char vals[VB ? T * VB : 16];
+    uint16_t perm[T];
+};
+
+// bin_jobs: the job indices, grouped by size class (classes in order).
+template <int KB>
+__global__ void k_bin_jobs(Ws ws) {
+    if (has_error(ws.ctr)) return;
+    constexpr int NC = FinishClasses<KB>::kCount;
+    uint32_t base[NC];
+    uint32_t run = 0;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+        base[c] = run;
+        run += ws.ctr->class_count[c];
+    }
+    const uint32_t nj = min(ws.ctr->njobs, ws.jcap);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nj; j += gridDim.x * blockDim.x) {
+        const int c = finish_class<KB>(ws.jobs[j].len);
+        const uint32_t at = base[c] + atomicAdd(&ws.ctr->class_cursor[c], 1u);
+        if (at < ws.jcap) ws.jobidx[at] = j;
+    }
+}
+
+// AND / OR of the job's encoded keys across the CTA (k-wide keys reduce only
+// their live 32-bit words).
+template <int KB>
+__device__ __forceinline__ void block_and_or(typename KeyTraits<KB>::Bits &a,
+                                             typename KeyTraits<KB>::Bits &o, uint4 *sand,
+                                             uint4 *sor) {
+    using KT = KeyTraits<KB>;
+    constexpr int NW = KB / 4;
+    uint4 pa = KT::pack(a), po = KT::pack(o);
+    uint32_t *xa = &pa.x, *xo = &po.x;
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NW; q++) {
+            xa[q] &= __shfl_xor_sync(0xffffffffu, xa[q], o2);
+            xo[q] |= __shfl_xor_sync(0xffffffffu, xo[q], o2);
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sand[w] = pa;
+        sor[w] = po;
+    }
+    __syncthreads();
+    uint4 ra = sand[0], ro = sor[0];
+    for (int i = 1; i < kWarps; i++) {
+        ra.x &= sand[i].x; ra.y &= sand[i].y; ra.z &= sand[i].z; ra.w &= sand[i].w;
+        ro.x |= sor[i].x; ro.y |= sor[i].y; ro.z |= sor[i].z; ro.w |= sor[i].w;
+    }
+    a = KT::unpack(ra);
+    o = KT::unpack(ro);
+}
+
+// The fast path for one job of len <= kThreads * IU keys staged in shared
+// memory.  Returns false if the job's runs are too long (the job then goes to
+// the LSD path untouched).
+template <int KB, int VB, int IU>
+__device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws &ws,
+                                            const Encoder<KB> &enc, const Decoder<KB> &dec,
+                                            const Job &job, typename KeyTraits<KB>::Raw *dst,
+                                            typename ValTraits<VB>::T *vdst) {
+    using KT = KeyTraits<KB>;
+    using Raw = typename KT::Raw;
+    using Bits = typename KT::Bits;
+    using V = typename ValTraits<VB>::T;
+    constexpr int W = KT::kW;
+    Raw *skeys = reinterpret_cast<Raw *>(s.keys);
+    V *svals = reinterpret_cast<V *>(s.vals);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int len = (int)job.len;
+    FinishFastSmem &fs = s.u.fast;
+    for (int i = tid; i < kFinishBins / 2; i += kThreads) fs.cnt2[i] = 0;
+    if (tid == 0) fs.maxrun = 0;
+
+    // encode once, in registers; AND / OR of the job
+    Bits e[IU];
+    Bits a = KT::ones(), o = KT::zero();
+#pragma unroll
+    for (int k = 0; k < IU; k++) {
+        const int i = k * kThreads + tid;
+        if (i < len) {
+            e[k] = enc(skeys[i]);
+            a = a & e[k];
+            o = o | e[k];
+        }
+    }
+    block_and_or<KB>(a, o, s.sand, s.sor);
+    const int f = KT::first_diff(a, o);
+    if (f >= W) {
+        // all keys equal: already in order
+        if (job.buf == 1) {
+            for (int i = tid; i < len; i += kThreads) {
+                dst[i] = skeys[i];
+                if (VB) vdst[i] = svals[i];
+            }
+        }
+        return true;
+    }
+
+    // unstable 12-bit split at f: one shared-memory atomic per key
+    uint32_t dr[IU];   // (digit << 16) | rank within the digit
+#pragma unroll
+    for (int k = 0; k < IU; k++) {
+        const int i = k * kThreads + tid;
+        const bool valid = i < len;
+        const uint32_t d = valid ? KT::bits_at(e[k], f, kFinishBits) : 0u;
+        const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+        const uint32_t sh = (d & 1) * 16;
+        uint32_t r = 0;
+        if (__all_sync(0xffffffffu, valid && d == d0)) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&fs.cnt2[d0 >> 1], 32u << sh);
+            r = ((__shfl_sync(0xffffffffu, c, 0) >> sh) & 0xffffu) + lane;
+        } else if (valid) {
+            r = (atomicAdd(&fs.cnt2[d >> 1], 1u << sh) >> sh) & 0xffffu;
+        }
+        dr[k] = (d << 16) | r;
+    }
+    __syncthreads();
+    {
+        constexpr int PW = kFinishBins / 2 / kThreads;   // words per thread
+        uint32_t c[PW], sum = 0, mx = 0;
+#pragma unroll
+        for (int q = 0; q < PW; q++) {
+            c[q] = fs.cnt2[tid * PW + q];
+            const uint32_t lo = c[q] & 0xffffu, hi = c[q] >> 16;
+            sum += lo + hi;
+            mx = max(mx, max(lo, hi));
+        }
+        uint32_t total;
+        uint32_t run = block_exclusive_scan(sum, fs.scratch, &total);
+#pragma unroll
+        for (int q = 0; q < PW; q++) {
+            const uint32_t lo = run;
+            run += c[q] & 0xffffu;
+            fs.start2[tid * PW + q] = lo | (run << 16);
+            run += c[q] >> 16;
+        }
+        if (mx > kFinishRun) atomicMax(&fs.maxrun, mx);
+    }
+    __syncthreads();
+    if (fs.maxrun > (uint32_t)kFinishRun) return false;
+
+    // place the encoded keys in split order (over the raw keys, all read), with
+    // their input positions
+    Bits *senc = reinterpret_cast<Bits *>(s.keys);
+#pragma unroll
+    for (int k = 0; k < IU; k++) {
+        const int i = k * kThreads + tid;
+        if (i < len) {
+            const uint32_t at = half16(fs.start2, dr[k] >> 16) + (dr[k] & 0xffffu);
+            if (at < (uint32_t)len) {
+                senc[at] = e[k];
+                s.perm[at] = (uint16_t)i;
+            } else {
+                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+            }
+        }
+    }
+    __syncthreads();
+    // every key's place in its run: the run's keys that precede it in (encoded
+    // key, input position) order; a fixed compare against the first four run
+    // members, a loop for longer runs (rare); written straight to the output
+#pragma unroll
+    for (int k = 0; k < IU; k++) {
+        const int x = k * kThreads + tid;
+        if (x < len) {
+            const Bits ex = senc[x];
+            const uint32_t ix = s.perm[x];
+            const uint32_t d = KT::bits_at(ex, f, kFinishBits);
+            const int b0 = (int)half16(fs.start2, d), m = (int)half16(fs.cnt2, d);
+            int rank = 0;
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int y = min(b0 + t, len - 1);
+                const Bits ey = senc[y];
+                const uint32_t iy = s.perm[y];
+                rank += ((t < m) && (KT::less(ey, ex) || (!KT::less(ex, ey) && iy < ix))) ? 1 : 0;
+            }
+            for (int y = b0 + 4; y < b0 + m; y++) {
+                const Bits ey = senc[y];
+                const uint32_t iy = s.perm[y];
+                rank += (KT::less(ey, ex) || (!KT::less(ex, ey) && iy < ix)) ? 1 : 0;
+            }
+            const int at = min(b0 + rank, len - 1);
+            dst[at] = dec(ex);
+            if (VB) vdst[at] = svals[ix];
+        }
+    }
+    return true;
+}
+
+template <int KB, int VB, int CLS>
+__global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2)
+    k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
+    using KT = KeyTraits<KB>;
+    using Raw = typename KT::Raw;
+    using V = typename ValTraits<VB>::T;
+    constexpr int IU = FinishClasses<KB>::iu(CLS);
+    constexpr int W = KT::kW;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto &s = *reinterpret_cast<FinishSmem<KB, VB, IU> *>(smem_raw);
+    Raw *skeys = reinterpret_cast<Raw *>(s.keys);
+    V *svals = reinterpret_cast<V *>(s.vals);
+    if (has_error(ws.ctr)) return;
+    const Encoder<KB> enc(p.map);
+    const Decoder<KB> dec(p.map);
+    uint32_t base = 0;
+    for (int c = 0; c < CLS; c++) base += ws.ctr->class_count[c];
+    const uint32_t count = ws.ctr->class_count[CLS];
+    if (count == 0 || base + count > ws.jcap) return;
+    const uint32_t *mine = ws.jobidx + base;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
+        s.next_ticket = t;
+        if (t < count) s.next_job = ws.jobs[mine[t]];
+    }
+    for (;;) {
+        __syncthreads();
+        const uint32_t jt = s.next_ticket;
+        if (jt >= count) break;
+        const Job job = s.next_job;
+        __syncthreads();
+        const int len = (int)job.len;
+        const Raw *src = reinterpret_cast<const Raw *>(job.buf ? keys1 : keys0) + job.begin;
+        Raw *dst = reinterpret_cast<Raw *>(keys0) + job.begin;
+        const V *vsrc = VB ? reinterpret_cast<const V *>(job.buf ? vals1 : vals0) + job.begin : nullptr;
+        V *vdst = VB ? reinterpret_cast<V *>(vals0) + job.begin : nullptr;
+        const bool trivial = job.pos >= W || len <= 1 || len > kThreads * IU;
+        if (!trivial) {
+            for (int i = tid; i < len; i += kThreads) {
+                cp_async<KB>(&skeys[i], &src[i]);
+                if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
+            }
+        }
+        if (tid == 0) {   // the next job, while this one's data arrives
+            const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
+            s.next_ticket = t;
+            if (t < count) s.next_job = ws.jobs[mine[t]];
+        }
+        if (trivial) {
+            if (len > kThreads * IU) {
+                if (tid == 0) set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+            } else if (job.buf == 1) {
+                for (int i = tid; i < len; i += kThreads) {
+                    dst[i] = src[i];
+                    if (VB) vdst[i] = vsrc[i];
+                }
+            }
+            continue;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (!finish_fast<KB, VB, IU>(s, ws, enc, dec, job, dst, vdst) && tid == 0) {
+            // runs too long for the fast path: the job goes to the LSD path
+            const uint32_t ji = atomicAdd(&ws.ctr->njobs2, 1u);
+            if (ji < ws.jcap) ws.jobs2[ji] = job;
+            else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// finish_lsd: the jobs whose runs were too long for the fast path (heavy
+// duplication), sorted by an LSD radix sort over 8-bit windows: the last
+// window starts at pos and may overlap the one below it, windows whose bits
+// are equal across the job are skipped, every pass is stable except the first
+// one of a key-only sort.  The passes refine perm[sorted position] = input
+// position over the keys and payloads staged in shared memory.
+// ---------------------------------------------------------------------------
+template <int KB, int VB>
+struct FinishLsdSmem {
+    static constexpr int T = TileShape<KB>::kTile;
+    RankSmem rank;
     uint4 sand[kWarps], sor[kWarps];
     uint32_t ticket;
     alignas(16) unsigned char keys[T * KB];
@@ -848,8 +1168,8 @@ struct FinishSmem {
 };
 
 template <int KB, int VB>
-__global__ void __launch_bounds__(kThreads, VB == 0 ? 3 : 2)
-    k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
+__global__ void __launch_bounds__(kThreads, 2)
+    k_finish_lsd(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
@@ -857,34 +1177,25 @@ __global__ void __launch_bounds__(kThreads, VB == 0 ? 3 : 2)
     constexpr int ITEMS = TileShape<KB>::kItems;
     constexpr int W = KT::kW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &s = *reinterpret_cast<FinishSmem<KB, VB> *>(smem_raw);
+    auto &s = *reinterpret_cast<FinishLsdSmem<KB, VB> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
     const Encoder<KB> enc(p.map);
-    const uint32_t njobs = min(ws.ctr->njobs, ws.jcap);
+    const uint32_t njobs = min(ws.ctr->njobs2, ws.jcap);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (;;) {
-        if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_fin, 1u);
+        if (tid == 0) s.ticket = atomicAdd(&ws.ctr->ticket_fin2, 1u);
         __syncthreads();
         const uint32_t jt = s.ticket;
         __syncthreads();
         if (jt >= njobs) break;
-        const Job job = ws.jobs[jt];
+        const Job job = ws.jobs2[jt];
         const int len = (int)job.len;
         const Raw *src = reinterpret_cast<const Raw *>(job.buf ? keys1 : keys0) + job.begin;
         Raw *dst = reinterpret_cast<Raw *>(keys0) + job.begin;
         const V *vsrc = VB ? reinterpret_cast<const V *>(job.buf ? vals1 : vals0) + job.begin : nullptr;
         V *vdst = VB ? reinterpret_cast<V *>(vals0) + job.begin : nullptr;
-        if (job.pos >= W || len <= 1) {
-            if (job.buf == 1) {
-                for (int i = tid; i < len; i += kThreads) {
-                    dst[i] = src[i];
-                    if (VB) vdst[i] = vsrc[i];
-                }
-            }
-            continue;
-        }
         for (int i = tid; i < len; i += kThreads) {
             cp_async<KB>(&skeys[i], &src[i]);
             if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
@@ -913,9 +1224,6 @@ __global__ void __launch_bounds__(kThreads, VB == 0 ? 3 : 2)
             s.sand[w] = pa;
             s.sor[w] = po;
         }
-        FinishFastSmem &fs = s.u.fast;
-        for (int i = tid; i < kFinishBins; i += kThreads) fs.cnt[i] = 0;
-        if (tid == 0) fs.maxrun = 0;
         __syncthreads();
         uint4 ra = s.sand[0], ro = s.sor[0];
         for (int i = 1; i < kWarps; i++) {
@@ -923,140 +1231,51 @@ __global__ void __launch_bounds__(kThreads, VB == 0 ? 3 : 2)
             ro.x |= s.sor[i].x; ro.y |= s.sor[i].y; ro.z |= s.sor[i].z; ro.w |= s.sor[i].w;
         }
         const Bits diff_a = KT::unpack(ra), diff_o = KT::unpack(ro);
-        const int f = KT::first_diff(diff_a, diff_o);
-        if (f >= W) {
-            // all keys equal: already in order
-            if (job.buf == 1) {
-                for (int i = tid; i < len; i += kThreads) {
-                    dst[i] = skeys[i];
-                    if (VB) vdst[i] = svals[i];
-                }
-            }
-            __syncthreads();
-            continue;
-        }
-
-        // ---- fast path: unstable 11-bit split at f ----
-        uint32_t dr[ITEMS];   // (digit << 16) | rank within the digit
+        const int iu = (len + kThreads - 1) / kThreads;
+        int q = W - kBits;
+        bool moved = false;
+        Packed<ITEMS> pk;
+        uint32_t src_pos[(ITEMS + 1) / 2];
+        for (;;) {
+            const int qq = q > (int)job.pos ? q : (int)job.pos;
+            const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
+            if (varies) {
+                __syncthreads();
 #pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            if (k * kThreads < len) {
-                const int i = k * kThreads + tid;
-                const bool valid = i < len;
-                const uint32_t d = valid ? KT::bits_at(enc(skeys[i]), f, kFinishBits) : 0u;
-                const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
-                uint32_t r = 0;
-                if (__all_sync(0xffffffffu, valid && d == d0)) {
-                    uint32_t c = 0;
-                    if (lane == 0) c = atomicAdd(&fs.cnt[d0], 32u);
-                    r = __shfl_sync(0xffffffffu, c, 0) + lane;
-                } else if (valid) {
-                    r = atomicAdd(&fs.cnt[d], 1u);
-                }
-                dr[k] = (d << 16) | r;
-            }
-        }
-        __syncthreads();
-        {
-            constexpr int PER = kFinishBins / kThreads;
-            uint32_t c[PER], sum = 0, mx = 0;
-#pragma unroll
-            for (int q = 0; q < PER; q++) {
-                c[q] = fs.cnt[tid * PER + q];
-                sum += c[q];
-                mx = max(mx, c[q]);
-            }
-            uint32_t total;
-            uint32_t run = block_exclusive_scan(sum, fs.scratch, &total);
-#pragma unroll
-            for (int q = 0; q < PER; q++) {
-                fs.start[tid * PER + q] = run;
-                run += c[q];
-            }
-            if (mx > kFinishRun) atomicMax(&fs.maxrun, mx);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < ITEMS; k++) {
-            const int i = k * kThreads + tid;
-            if (k * kThreads < len && i < len) {
-                const uint32_t at = fs.start[dr[k] >> 16] + (dr[k] & 0xffffu);
-                if (at < (uint32_t)len) s.perm[at] = (uint16_t)i;
-                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-            }
-        }
-        __syncthreads();
-        if (fs.maxrun <= (uint32_t)kFinishRun) {
-            // every key's place in its run: the run's keys that precede it in
-            // (encoded key, input position) order; written straight to the output
-#pragma unroll 4
-            for (int x = tid; x < len; x += kThreads) {
-                const uint32_t i = s.perm[x];
-                const Bits ki = enc(skeys[i]);
-                const uint32_t d = KT::bits_at(ki, f, kFinishBits);
-                const int b0 = (int)fs.start[d], m = (int)fs.cnt[d];
-                int rank = 0;
-                for (int y = b0; y < b0 + m; y++) {
-                    const uint32_t j = s.perm[y];
-                    const Bits kj = enc(skeys[j]);
-                    rank += (KT::less(kj, ki) || (!KT::less(ki, kj) && j < i)) ? 1 : 0;
-                }
-                const int at = min(b0 + rank, len - 1);
-                dst[at] = skeys[i];
-                if (VB) vdst[at] = svals[i];
-            }
-            __syncthreads();
-            continue;
-        }
-
-        // ---- fallback: stable LSD over 8-bit windows, from the input order ----
-        {
-            const int iu = (len + kThreads - 1) / kThreads;
-            int q = W - kBits;
-            bool moved = false;
-            Packed<ITEMS> pk;
-            uint32_t src_pos[(ITEMS + 1) / 2];
-            for (;;) {
-                const int qq = q > (int)job.pos ? q : (int)job.pos;
-                const bool varies = KT::digit(diff_a, qq) != KT::digit(diff_o, qq);
-                if (varies) {
-                    __syncthreads();
-#pragma unroll
-                    for (int j = 0; j < ITEMS; j++) {
-                        if (j < iu) {
-                            const int i = striped(iu, j);
-                            uint32_t x = 0;
-                            if (i < len) x = moved ? s.perm[i] : (uint32_t)i;
-                            if (x >= (uint32_t)len) {
-                                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                                x = 0;
-                            }
-                            if ((j & 1) == 0) src_pos[j >> 1] = x;
-                            else src_pos[j >> 1] |= x << 16;
-                            pk.set_dig(j, i < len ? KT::digit(enc(skeys[x]), qq) : 0u);
+                for (int j = 0; j < ITEMS; j++) {
+                    if (j < iu) {
+                        const int i = striped(iu, j);
+                        uint32_t x = 0;
+                        if (i < len) x = moved ? s.perm[i] : (uint32_t)i;
+                        if (x >= (uint32_t)len) {
+                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                            x = 0;
                         }
+                        if ((j & 1) == 0) src_pos[j >> 1] = x;
+                        else src_pos[j >> 1] |= x << 16;
+                        pk.set_dig(j, i < len ? KT::digit(enc(skeys[x]), qq) : 0u);
                     }
-                    if (VB || moved) rank_stable<ITEMS>(pk, iu, len, s.u.rank);
-                    else rank_unstable<ITEMS>(pk, iu, len, s.u.rank);
-#pragma unroll
-                    for (int j = 0; j < ITEMS; j++) {
-                        if (j < iu && striped(iu, j) < len) {
-                            const uint32_t r = pk.rank(j);
-                            if (r < (uint32_t)len)
-                                s.perm[r] = (uint16_t)(src_pos[j >> 1] >> ((j & 1) * 16));
-                            else
-                                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                        }
-                    }
-                    moved = true;
                 }
-                if (qq == (int)job.pos) break;
-                q -= kBits;
+                if (VB || moved) rank_stable<ITEMS>(pk, iu, len, s.rank);
+                else rank_unstable<ITEMS>(pk, iu, len, s.rank);
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    if (j < iu && striped(iu, j) < len) {
+                        const uint32_t r = pk.rank(j);
+                        if (r < (uint32_t)len)
+                            s.perm[r] = (uint16_t)(src_pos[j >> 1] >> ((j & 1) * 16));
+                        else
+                            set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                    }
+                }
+                moved = true;
             }
+            if (qq == (int)job.pos) break;
+            q -= kBits;
         }
         __syncthreads();
         for (int x = tid; x < len; x += kThreads) {
-            const int i = min((int)s.perm[x], len - 1);
+            const int i = moved ? min((int)s.perm[x], len - 1) : x;
             dst[x] = skeys[i];
             if (VB) vdst[x] = svals[i];
         }
@@ -1074,7 +1293,7 @@ __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *key
                                                    void *vals1) {
     using Raw = typename KeyTraits<KB>::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int T = TileShape<KB>::kTile;
+    constexpr int T = PartShape<KB>::kTile;
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
     const unsigned long long ca = ws.ctr->copy_alloc;

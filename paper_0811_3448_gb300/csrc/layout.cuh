@@ -49,11 +49,13 @@ int launch(const char *name, int index, cudaStream_t s, F &&f) {
 // ---------------------------------------------------------------------------
 constexpr int kMinCutoff = 2048;
 
-inline int tile_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
+// keys per partition tile, and the finisher's largest job (= the largest cutoff)
+inline int tile_for(int kb) { return kb == 4 ? 4096 : 2048; }
+inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
 inline int levels_for(int kb) { return 8 * kb / kBits; }
 
 struct Layout {
-    size_t ctr, altk, altv, list[2], hist[2], andor[2], tilemap, cells, jobs, copies, total;
+    size_t ctr, altk, altv, list[2], hist[2], andor[2], tilemap, cells, jobs, jobidx, jobs2, copies, total;
     uint32_t mcap, tcap, jcap, ccap;
 };
 
@@ -88,6 +90,8 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     L.tilemap = take((size_t)t * sizeof(uint32_t));
     L.cells = take((size_t)t * kRadix * sizeof(uint32_t));
     L.jobs = take((size_t)j * sizeof(Job));
+    L.jobidx = take((size_t)j * sizeof(uint32_t));
+    L.jobs2 = take((size_t)j * sizeof(Job));
     L.copies = take((size_t)c * sizeof(CopyJob));
     L.total = o;
     return L;
@@ -107,6 +111,8 @@ inline Ws carve(const Layout &L, void *base) {
     ws.tilemap = reinterpret_cast<uint32_t *>(b + L.tilemap);
     ws.cells = reinterpret_cast<uint32_t *>(b + L.cells);
     ws.jobs = reinterpret_cast<Job *>(b + L.jobs);
+    ws.jobidx = reinterpret_cast<uint32_t *>(b + L.jobidx);
+    ws.jobs2 = reinterpret_cast<Job *>(b + L.jobs2);
     ws.copies = reinterpret_cast<CopyJob *>(b + L.copies);
     ws.mcap = L.mcap;
     ws.tcap = L.tcap;
