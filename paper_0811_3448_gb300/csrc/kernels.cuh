@@ -413,47 +413,45 @@ static __global__ void k_prep(Ws ws, int slot) {
 
 // ---------------------------------------------------------------------------
 // hist: per bucket of the level, counts of the digit at the bucket's bit
-// position and the AND / OR of its encoded keys.  Persistent CTAs take tiles
-// by ticket.
+// position and the AND / OR of its encoded keys.  Persistent CTAs take groups
+// of kHistGroup consecutive tiles by ticket, count into per-warp shared
+// histograms, and flush to the bucket (global atomics) only when the bucket
+// changes or the group ends.
 // ---------------------------------------------------------------------------
+constexpr int kHistGroup = 8;
+
 template <int KB>
 __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
     constexpr int T = PartShape<KB>::kTile;
-    __shared__ uint32_t sh[kRadix];
+    __shared__ uint32_t sh[kWarps][kRadix];
     __shared__ uint4 sand[kWarps], sor[kWarps];
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
     const Encoder<KB> enc(p.map);
-    const unsigned long long alloc = ws.ctr->alloc[slot];
+    const Bucket *list = slot ? ws.list[1] : ws.list[0];
+    uint32_t *hist = slot ? ws.hist[1] : ws.hist[0];
+    uint4 *andor = slot ? ws.andor[1] : ws.andor[0];
+    const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    for (;;) {
-        if (tid == 0) sticket = atomicAdd(&ws.ctr->ticket_hist, 1u);
-        sh[tid] = 0;
+    uint32_t *wh = sh[w];
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
+    Bits a = KT::ones(), o = KT::zero();
+    uint32_t cur_b = 0xffffffffu;   // bucket being accumulated (uniform across the CTA)
+
+    // flush the accumulated counts and AND / OR into bucket cur_b
+    auto flush = [&]() {
         __syncthreads();
-        const uint32_t t = sticket;
-        if (t >= nt) break;
-        const uint32_t b = ws.tilemap[t];
-        const Bucket bk = ws.list[slot][b];
-        if (bk.flags & (kHasHist | kSkip)) {
-            __syncthreads();
-            continue;
+        uint32_t c = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ww++) {
+            c += sh[ww][tid];
+            sh[ww][tid] = 0;
         }
-        const long long tb = bk.begin + (long long)(t - bk.tile_start) * T;
-        const int tlen = (int)min((long long)T, bk.begin + (long long)bk.len - tb);
-        const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
-        Bits a = KT::ones(), o = KT::zero();
-        for (int i = tid; i < tlen; i += kThreads) {
-            const Bits x = enc(src[i]);
-            a = a & x;
-            o = o | x;
-            const uint32_t d = KT::digit(x, bk.pos);
-            atomicAdd(&sh[d], 1u);
-        }
-        // AND / OR: warp reduce, then one thread per CTA updates the bucket
+        if (c) atomicAdd(&hist[(size_t)cur_b * kRadix + tid], c);
         uint4 pa = KT::pack(a), po = KT::pack(o);
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
@@ -477,17 +475,46 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
                 ra.x &= sand[i].x; ra.y &= sand[i].y; ra.z &= sand[i].z; ra.w &= sand[i].w;
                 ro.x |= sor[i].x; ro.y |= sor[i].y; ro.z |= sor[i].z; ro.w |= sor[i].w;
             }
-            uint32_t *ga = reinterpret_cast<uint32_t *>(&ws.andor[slot][2 * b]);
-            uint32_t *go = reinterpret_cast<uint32_t *>(&ws.andor[slot][2 * b + 1]);
+            uint32_t *ga = reinterpret_cast<uint32_t *>(&andor[2 * cur_b]);
+            uint32_t *go = reinterpret_cast<uint32_t *>(&andor[2 * cur_b + 1]);
             atomicAnd(ga + 0, ra.x); atomicAnd(ga + 1, ra.y);
             atomicAnd(ga + 2, ra.z); atomicAnd(ga + 3, ra.w);
             atomicOr(go + 0, ro.x); atomicOr(go + 1, ro.y);
             atomicOr(go + 2, ro.z); atomicOr(go + 3, ro.w);
         }
-        const uint32_t c = sh[tid];
-        if (c) atomicAdd(&ws.hist[slot][(size_t)b * kRadix + tid], c);
+        a = KT::ones();
+        o = KT::zero();
+    };
+
+    for (;;) {
+        if (tid == 0) sticket = atomicAdd(&ws.ctr->ticket_hist, 1u);
         __syncthreads();
+        const uint32_t g = sticket;
+        __syncthreads();
+        const uint32_t t0 = g * kHistGroup;
+        if (t0 >= nt) break;
+        const uint32_t t1 = min(t0 + kHistGroup, nt);
+        for (uint32_t t = t0; t < t1; t++) {
+            const uint32_t b = ws.tilemap[t];
+            const Bucket bk = list[b];
+            if (bk.flags & (kHasHist | kSkip)) continue;
+            if (b != cur_b) {
+                if (cur_b != 0xffffffffu) flush();
+                cur_b = b;
+            }
+            const long long tb = bk.begin + (long long)(t - bk.tile_start) * T;
+            const int tlen = (int)min((long long)T, bk.begin + (long long)bk.len - tb);
+            const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
+#pragma unroll 4
+            for (int i = tid; i < tlen; i += kThreads) {
+                const Bits x = enc(src[i]);
+                a = a & x;
+                o = o | x;
+                atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+            }
+        }
     }
+    if (cur_b != 0xffffffffu) flush();
 }
 
 // ---------------------------------------------------------------------------
@@ -512,6 +539,11 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     __shared__ uint32_t sexcl[kRadix];
     __shared__ uint32_t scratch[kWarps];
     __shared__ unsigned long long sbase;
+    __shared__ Job sjobs[kRadix];            // this parent's finisher jobs
+    __shared__ CopyJob scopies[kRadix];      // and copy jobs (tile_start relative)
+    __shared__ uint32_t snjobs, sncopies, scopy_tiles;
+    __shared__ uint32_t sjob_base;
+    __shared__ unsigned long long scopy_base;
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nb = (uint32_t)alloc;
@@ -603,8 +635,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 ws.list[next][bi] = nbk;
             }
         }
-        // small and finished children: runs, by one thread in digit order
+        // small and finished children: runs, by one thread in digit order, into
+        // shared lists that are then reserved and written by the whole CTA
         if (tid == 0) {
+            snjobs = 0;
+            sncopies = 0;
+            scopy_tiles = 0;
             const uint32_t C = (uint32_t)p.cutoff;
             const uint32_t own = C / 8;       // a child this large is a job of its own
             long long run_begin = -1;
@@ -620,7 +656,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 j.pos = (uint16_t)jpos;
                 j.buf = (uint8_t)cbuf;
                 j.pad = 0;
-                push_job<KB>(ws, j);
+                sjobs[snjobs++] = j;
             };
             (void)run_child_pos;
             for (int d = 0; d < kRadix; d++) {
@@ -633,19 +669,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                     emit(run_begin, run_len, run_children);
                     run_begin = -1; run_len = 0; run_children = 0;
                     if (cbuf == 1) {
-                        const uint32_t tl = (c + T - 1) / T;
-                        const unsigned long long got = atomicAdd(
-                            &ws.ctr->copy_alloc, ((unsigned long long)tl << 32) | 1ull);
-                        const uint32_t ci = (uint32_t)got;
-                        if (ci >= ws.ccap) {
-                            set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
-                        } else {
-                            CopyJob cj;
-                            cj.begin = cb;
-                            cj.len = c;
-                            cj.tile_start = (uint32_t)(got >> 32);
-                            ws.copies[ci] = cj;
-                        }
+                        CopyJob cj;
+                        cj.begin = cb;
+                        cj.len = c;
+                        cj.tile_start = scopy_tiles;
+                        scopies[sncopies++] = cj;
+                        scopy_tiles += (c + T - 1) / T;
                     }
                     continue;
                 }
@@ -671,6 +700,28 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 }
             }
             emit(run_begin, run_len, run_children);
+            sjob_base = snjobs ? atomicAdd(&ws.ctr->njobs, snjobs) : 0u;
+            scopy_base = sncopies ? atomicAdd(&ws.ctr->copy_alloc,
+                                              ((unsigned long long)scopy_tiles << 32) | sncopies)
+                                  : 0ull;
+        }
+        __syncthreads();
+        if (tid < (int)snjobs) {
+            const Job j = sjobs[tid];
+            const uint32_t ji = sjob_base + tid;
+            if (ji < ws.jcap) {
+                ws.jobs[ji] = j;
+                atomicAdd(&ws.ctr->class_count[finish_class<KB>(j.len)], 1u);
+            } else {
+                set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+            }
+        }
+        if (tid < (int)sncopies) {
+            CopyJob cj = scopies[tid];
+            const uint32_t ci = (uint32_t)scopy_base + tid;
+            cj.tile_start += (uint32_t)(scopy_base >> 32);
+            if (ci < ws.ccap) ws.copies[ci] = cj;
+            else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
         }
         __syncthreads();
     }
