@@ -140,6 +140,27 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
                          int val_bytes, int pos, int bits, int64_t *d_offsets, void *d_ws,
                          size_t ws_bytes, const binar_config *cfg, void *stream);
 
+/* The partition pass of binar_partition_pass without a workspace argument:
+ * the library allocates nothing and uses 4 MiB of scratch memory that it
+ * declares itself (one fixed array per GPU that loads the library, kept until
+ * the process exits).  The paper has no counterpart; this exists for callers
+ * that cannot allocate or keep a workspace -- e.g. code that owns all device
+ * memory through a fixed pool with a hard budget, or a latency-critical loop
+ * that must not call (and synchronise on) cudaMalloc.
+ *   Arguments, layout and results as binar_partition_pass.
+ *   Limit: n <= about 16M keys of 4 bytes, about 8M keys of 8 or 16 bytes;
+ *   larger n returns BINAR_ERR_WORKSPACE_TOO_SMALL before any work.
+ *   The first call on a device looks up the scratch array's device address
+ *   (host-side set-up); make that first call before any stream capture.
+ *   Every call shares the one scratch array and each call resets what it
+ *   needs, so calls that overlap on the GPU (different streams, or threads)
+ *   race and must not be issued.  Device-side errors are recorded in the
+ *   shared scratch only; they are not readable by the caller. */
+int binar_partition_pass_noalloc(const void *d_keys_in, const void *d_vals_in, void *d_keys_out,
+                                 void *d_vals_out, int64_t n, int key_bytes, binar_key_map map,
+                                 int val_bytes, int pos, int bits, int64_t *d_offsets,
+                                 void *stream);
+
 /* Waits for `stream`, then reads the device status word of the workspace
  * into *out_status (a binar_status) and clears it.  Returns binar_status of
  * the query itself. */

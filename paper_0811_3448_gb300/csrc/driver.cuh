@@ -52,7 +52,7 @@ int run_call_vb(const Call &c) {
     const int L = levels_for(KB);
     const int sms = device_sms();
     if (sms <= 0) return BINAR_ERR_CUDA;
-    const Layout lay = make_layout(c.n, c.offsets ? c.num_segments : 1, KB, VB);
+    const Layout lay = c.layout ? *c.layout : make_layout(c.n, c.offsets ? c.num_segments : 1, KB, VB);
     const Ws ws = carve(lay, c.ws);
     Params p{};
     p.map = c.map;

@@ -132,6 +132,7 @@ struct Call {
     long long *pass_offsets;
     int pass_pos;
     bool pass_mode;
+    const Layout *layout;          // workspace layout to use instead of make_layout(), or nullptr
     const long long *offsets;      // segmented: device offsets, else nullptr
     long long num_segments;
     long long n;
