@@ -46,6 +46,14 @@ def parse_args():
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--workload", choices=["pairs", "segments", "serve"], default="pairs",
+                    help="pairs: 256M uint32+uint32 sort (the headline); segments: 20,000 "
+                         "segments in one CUDA-graph launch vs one call per segment; serve: "
+                         "the continuous-batching request loop vs one request per launch")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
+    ap.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
     return ap.parse_args()
 
 
@@ -346,10 +354,104 @@ def run_binar(args):
         dist.destroy_process_group()
 
 
+def run_segments(args):
+    """Config 4: 20,000 log-uniform segments (~256M uint32 keys, uint32 payload =
+    index within the segment), the whole segmented sort captured as one CUDA
+    graph and replayed; compared with one binar_sort_pairs call per segment."""
+    import torch
+    from paper_0811_3448_gb300 import autotune, binding, inputs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    sizes = inputs.config4_segment_sizes(total=args.n, count=20000)
+    off_h = inputs.offsets_from_sizes(sizes)
+    n = int(off_h[-1])
+    keys_h = inputs.uniform_keys(n, np.uint32, inputs.rng(4, 1))
+    vals_h = inputs.segment_index_payload(off_h)
+    dev = torch.device("cuda", local)
+    off = torch.from_numpy(off_h).to(dev)
+    k0 = torch.from_numpy(keys_h).to(dev)
+    v0 = torch.from_numpy(vals_h).to(dev)
+    k, v = k0.clone(), v0.clone()
+    segs = len(off_h) - 1
+    cfg, timings = autotune.tune(k0, v0, off)
+    ws = binding.workspace(n, 4, 4, segs, device=dev)
+    binding.sort_segmented(k, off, v, ws=ws, config=cfg)      # set-up before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            binding.sort_segmented(k, off, v, ws=ws, config=cfg)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        k.copy_(k0)
+        v.copy_(v0)
+        graph.replay()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        k.copy_(k0)
+        v.copy_(v0)
+        evs[i][0].record(stream)
+        graph.replay()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    binding.check_status(ws)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    # the plain form: one sort call per segment
+    k.copy_(k0)
+    v.copy_(v0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for s_ in range(segs):
+        a, b = int(off_h[s_]), int(off_h[s_ + 1])
+        if b - a >= 2:
+            binding.sort_pairs(k[a:b], v[a:b], ws=ws)
+    e1.record(stream)
+    e1.synchronize()
+    plain_wall = time.perf_counter() - t0
+    plain_ms = e0.elapsed_time(e1)
+    binding.check_status(ws)
+    out = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic",
+           "config": {"workload": "20,000 segments, log-uniform sizes in [1, 2^20] rescaled to "
+                                  f"{n} uint32 keys + uint32 payload, one CUDA-graph launch",
+                      "segments": segs, "n": n, "parallelism": f"replicas x{world}",
+                      "l2": "1 GiB keys + 1 GiB payloads restored before every replay"},
+           "autotuned": {"small_cutoff": cfg.small_cutoff, "ctas_per_sm": cfg.ctas_per_sm,
+                         "timings_ms": timings},
+           "plain_per_segment": {"value": n / (plain_ms * 1e-3) / 1e9, "unit": UNIT,
+                                 "ms": plain_ms, "wall_s": plain_wall, "calls": segs},
+           "clocks": sampler.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "segments":
+        run_segments(args)
+    elif args.workload == "serve":
+        from paper_0811_3448_gb300 import serve
+        sampler = ClockSampler(dist_env()[2])
+        sampler.start()
+        line = serve.bench_main(args)
+        sampler.stop()
+        if line is not None:
+            line["clocks"] = sampler.summary()
+            print(json.dumps(line), flush=True)
     else:
         run_binar(args)
 

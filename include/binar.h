@@ -13,7 +13,8 @@
  *
  * Conventions shared by every call:
  *  - Device pointers are CUDA device addresses; the caller owns all memory.
- *    Key, payload and workspace pointers must be 16-byte aligned.
+ *    Keys and payloads must be aligned to their element size (key_bytes,
+ *    val_bytes); the workspace must be 16-byte aligned.
  *  - Sorting is in place on the caller's buffers (as the paper's algorithm
  *    is, "Space Analysis"), using a caller-provided workspace of
  *    binar_workspace_bytes() bytes for the out-of-place passes.
@@ -182,6 +183,20 @@ typedef struct {
 
 int binar_profile_start(void);
 int binar_profile_stop(binar_kernel_stat *out, int cap, int *count);
+
+/* Synthetic input on the device (no counterpart in the paper, which defines
+ * no input generator): writes n elements of `elem_bytes` (4, 8 or 16) to
+ * d_out, element i taken from SplitMix64 (Steele, Lea and Flood, OOPSLA
+ * 2014) used as a counter-based generator:
+ *   x(seed, i) = mix(seed + (i + 1) * 0x9E3779B97F4A7C15),
+ *   mix(z): z = (z ^ z>>30) * 0xBF58476D1CE4E5B9; z = (z ^ z>>27) * 0x94D049BB133111EB;
+ *           return z ^ z>>31.
+ * 4-byte elements are the low 32 bits of x(seed, i), 8-byte elements x(seed, i);
+ * 16-byte elements are x(seed, i) then x(seed ^ 0xD1B54A32D192ED03, i), each
+ * little-endian.  d_out must be aligned to elem_bytes.  Asynchronous on
+ * `stream`; the caller owns d_out.  Returns BINAR_ERR_INVALID_ARG for bad
+ * arguments, BINAR_ERR_CUDA if the launch fails. */
+int binar_generate(void *d_out, int64_t n, int elem_bytes, uint64_t seed, void *stream);
 
 /* Library version as "major.minor.patch". */
 const char *binar_version(void);

@@ -87,9 +87,10 @@ def load():
         lib.binar_profile_start.argtypes = []
         lib.binar_profile_stop.argtypes = [ctypes.POINTER(KernelStat), i32, ctypes.POINTER(i32)]
         lib.binar_version.restype = ctypes.c_char_p
+        lib.binar_generate.argtypes = [p, i64, i32, ctypes.c_uint64, p]
         for name in ("binar_workspace_bytes", "binar_sort_keys", "binar_sort_pairs",
                      "binar_sort_segmented", "binar_partition_pass", "binar_workspace_status",
-                     "binar_profile_start", "binar_profile_stop"):
+                     "binar_profile_start", "binar_profile_stop", "binar_generate"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -266,6 +267,21 @@ def profile_stop():
     _check(load().binar_profile_stop(arr, cap, ctypes.byref(cnt)), "binar_profile_stop")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms))
             for i in range(min(cnt.value, cap))}
+
+
+def generate(out: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Fills ``out`` (4-, 8- or 16-byte elements; uint8 (n, 16) for 16) with
+    SplitMix64 values of counters 0 .. n-1 (binar_generate)."""
+    _check_dev(out)
+    if out.dim() == 2 and out.dtype == torch.uint8 and out.shape[1] == 16:
+        n, eb = out.shape[0], 16
+    elif out.dim() == 1 and out.element_size() in (4, 8):
+        n, eb = out.shape[0], out.element_size()
+    else:
+        raise TypeError("generate: 1-D 4/8-byte tensor or uint8 (n, 16)")
+    _check(load().binar_generate(_ptr(out), n, eb, ctypes.c_uint64(seed & (2**64 - 1)),
+                                 _stream(stream)), "binar_generate")
+    return out
 
 
 def version() -> str:

@@ -93,6 +93,10 @@ using namespace binar;
 namespace {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+// keys and payloads need their natural alignment (the kernels move whole elements)
+bool aligned_to(const void *p, int bytes) {
+    return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(bytes - 1)) == 0;
+}
 
 int check_types(int key_bytes, int map, int val_bytes) {
     if (key_bytes != 4 && key_bytes != 8 && key_bytes != 16) return BINAR_ERR_INVALID_ARG;
@@ -160,8 +164,8 @@ static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int
     if (n < 0) return BINAR_ERR_INVALID_ARG;
     if (!d_offsets && n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_UNSUPPORTED;
     if (d_offsets && num_segments < 0) return BINAR_ERR_INVALID_ARG;
-    if (n > 0 && (!d_keys || !aligned16(d_keys))) return BINAR_ERR_INVALID_ARG;
-    if (val_bytes && n > 0 && (!d_vals || !aligned16(d_vals))) return BINAR_ERR_INVALID_ARG;
+    if (n > 0 && (!d_keys || !aligned_to(d_keys, key_bytes))) return BINAR_ERR_INVALID_ARG;
+    if (val_bytes && n > 0 && (!d_vals || !aligned_to(d_vals, val_bytes))) return BINAR_ERR_INVALID_ARG;
     if (!val_bytes && d_vals) return BINAR_ERR_INVALID_ARG;
     if (!d_ws || !aligned16(d_ws)) return BINAR_ERR_INVALID_ARG;
     const long long segs = d_offsets ? (num_segments > 0 ? num_segments : 1) : 1;
@@ -220,10 +224,12 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
     if (bits != 0 && bits != kBits) return BINAR_ERR_UNSUPPORTED;
     if (n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
     if (pos < 0 || pos >= 8 * key_bytes) return BINAR_ERR_INVALID_ARG;
-    if (n > 0 && (!d_keys_in || !d_keys_out || !aligned16(d_keys_in) || !aligned16(d_keys_out)))
+    if (n > 0 && (!d_keys_in || !d_keys_out || !aligned_to(d_keys_in, key_bytes) ||
+                  !aligned_to(d_keys_out, key_bytes)))
         return BINAR_ERR_INVALID_ARG;
     if (val_bytes && n > 0 &&
-        (!d_vals_in || !d_vals_out || !aligned16(d_vals_in) || !aligned16(d_vals_out)))
+        (!d_vals_in || !d_vals_out || !aligned_to(d_vals_in, val_bytes) ||
+         !aligned_to(d_vals_out, val_bytes)))
         return BINAR_ERR_INVALID_ARG;
     if (!d_ws || !aligned16(d_ws)) return BINAR_ERR_INVALID_ARG;
     if (ws_bytes < make_layout(n, 1, key_bytes, val_bytes).total)

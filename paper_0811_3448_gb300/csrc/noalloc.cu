@@ -87,7 +87,9 @@ Layout pass_layout(long long n, int kb) {
     return L;
 }
 
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+bool aligned_to(const void *p, int bytes) {
+    return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(bytes - 1)) == 0;
+}
 
 }  // namespace
 
@@ -101,10 +103,12 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     if (map == BINAR_MAP_FLOAT && key_bytes == 16) return BINAR_ERR_UNSUPPORTED;
     if (bits != 0 && bits != kBits) return BINAR_ERR_UNSUPPORTED;
     if (n < 0 || pos < 0 || pos >= 8 * key_bytes) return BINAR_ERR_INVALID_ARG;
-    if (n > 0 && (!d_keys_in || !d_keys_out || !aligned16(d_keys_in) || !aligned16(d_keys_out)))
+    if (n > 0 && (!d_keys_in || !d_keys_out || !aligned_to(d_keys_in, key_bytes) ||
+                  !aligned_to(d_keys_out, key_bytes)))
         return BINAR_ERR_INVALID_ARG;
     if (val_bytes && n > 0 &&
-        (!d_vals_in || !d_vals_out || !aligned16(d_vals_in) || !aligned16(d_vals_out)))
+        (!d_vals_in || !d_vals_out || !aligned_to(d_vals_in, val_bytes) ||
+         !aligned_to(d_vals_out, val_bytes)))
         return BINAR_ERR_INVALID_ARG;
     const Layout lay = pass_layout(n, key_bytes);
     if (lay.total > kScratchBytes) return BINAR_ERR_WORKSPACE_TOO_SMALL;   // n above the limit

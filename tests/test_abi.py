@@ -70,7 +70,7 @@ def _call_keys(lib, keys, n, kb, kmap, ws, wsb, cfg=None):
 
 def test_argument_checks_need_no_gpu(lib):
     aligned = ctypes.c_void_p(0x1000)
-    odd = ctypes.c_void_p(0x1004)
+    odd = ctypes.c_void_p(0x1002)
     big = 1 << 40
     # bad key width, bad map, FLOAT on 16-byte keys
     assert _call_keys(lib, aligned, 10, 3, 0, aligned, big) == binding.ERR_INVALID_ARG
@@ -80,6 +80,7 @@ def test_argument_checks_need_no_gpu(lib):
     assert _call_keys(lib, odd, 10, 4, 0, aligned, big) == binding.ERR_INVALID_ARG
     assert _call_keys(lib, None, 10, 4, 0, aligned, big) == binding.ERR_INVALID_ARG
     assert _call_keys(lib, aligned, 10, 4, 0, odd, big) == binding.ERR_INVALID_ARG
+    assert _call_keys(lib, ctypes.c_void_p(0x1004), 10, 8, 0, aligned, big) == binding.ERR_INVALID_ARG
     # negative n, too many keys, workspace too small
     assert _call_keys(lib, aligned, -1, 4, 0, aligned, big) == binding.ERR_INVALID_ARG
     assert _call_keys(lib, aligned, binding.MAX_BUCKET_KEYS + 1, 4, 0, aligned, big) == \
