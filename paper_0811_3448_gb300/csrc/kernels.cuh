@@ -25,10 +25,12 @@ template <int KB> struct TileShape {
     static constexpr int kItems = KB == 4 ? 32 : (KB == 8 ? 16 : 8);
     static constexpr int kTile = kThreads * kItems;
 };
-// Items per thread of a partition / histogram tile: 4096 / 2048 / 2048 keys.
+// Items per thread of a partition / histogram tile: 4096 / 2048 / 2048 keys;
+// resident partition CTAs per SM the register budget is sized for.
 template <int KB> struct PartShape {
     static constexpr int kItems = KB == 4 ? 16 : 8;
     static constexpr int kTile = kThreads * kItems;
+    static constexpr int kMinBlocks = KB == 16 ? 3 : 4;
 };
 
 // ---------------------------------------------------------------------------
@@ -194,6 +196,78 @@ __device__ __forceinline__ void rank_stable(Packed<ITEMS> &pk, int iu, int len, 
     }
 }
 
+// rank_stable_warp: the same stable ranking in one pass over the items.  Each
+// warp ranks its own items (a contiguous run of the tile, in processing
+// order) against per-warp digit counters -- peers found through the per-warp
+// lane mask as above -- so no counting pass is needed; afterwards the warps'
+// counts of every digit are scanned in warp order, offset by the digit's start
+// in the tile, and each item adds its warp's offset for its digit.
+// The per-warp lane masks must be zero on entry; they are left zero.
+template <int ITEMS>
+__device__ __forceinline__ void rank_stable_warp(Packed<ITEMS> &pk, int iu, int len, RankSmem &s) {
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const uint32_t lt = lanemask_lt();
+    uint32_t *wc = s.wcnt + w * kRadix;
+    uint32_t *wm = s.wmask + w * kRadix;
+#pragma unroll
+    for (int i = lane; i < kRadix; i += 32) wc[i] = 0;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        if (j < iu) {
+            const bool valid = striped(iu, j) < len;
+            const uint32_t d = pk.dig(j);
+            const uint32_t d0 = __shfl_sync(0xffffffffu, d, 0);
+            uint32_t rk;
+            if (__all_sync(0xffffffffu, valid && d == d0)) {
+                const uint32_t c = wc[d0];
+                rk = c + lane;
+                __syncwarp();
+                if (lane == 0) wc[d0] = c + 32;
+                __syncwarp();
+            } else {
+                if (valid) atomicOr(&wm[d], 1u << lane);
+                __syncwarp();
+                uint32_t peers = 0, c = 0;
+                if (valid) {
+                    peers = wm[d];
+                    c = wc[d];
+                }
+                rk = c + __popc(peers & lt);
+                __syncwarp();
+                if (valid && (peers >> lane) == 1u) {
+                    wc[d] = c + __popc(peers);
+                    wm[d] = 0;
+                }
+                __syncwarp();
+            }
+            pk.set_rank(j, rk);
+        }
+    }
+    __syncthreads();
+    {
+        const int d = tid;
+        uint32_t run = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ww++) {
+            const uint32_t c = s.wcnt[ww * kRadix + d];
+            s.wcnt[ww * kRadix + d] = run;
+            run += c;
+        }
+        s.dcount[d] = run;
+        uint32_t total;
+        const uint32_t start = block_exclusive_scan(run, s.scratch, &total);
+        s.dstart[d] = start;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ww++) s.wcnt[ww * kRadix + d] += start;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        if (j < iu) pk.add_rank(j, wc[pk.dig(j)]);
+    }
+}
+
 // rank_unstable: positions grouped by digit, arbitrary order inside a digit.
 // Enough for keys without payloads in an MSD pass (equal digits are split by
 // later passes, equal keys are indistinguishable) and for the first window of
@@ -234,7 +308,7 @@ __device__ __forceinline__ void rank_unstable(Packed<ITEMS> &pk, int iu, int len
 
 template <int ITEMS>
 __device__ __forceinline__ void rank_tile(Packed<ITEMS> &pk, int iu, int len, RankSmem &s) {
-    rank_stable<ITEMS>(pk, iu, len, s);
+    rank_stable_warp<ITEMS>(pk, iu, len, s);
 }
 template <int ITEMS>
 __device__ __forceinline__ void rank_tile(Packed<ITEMS> &pk, int iu, int len, RankSmemLite &s) {
@@ -744,32 +818,86 @@ static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long lon
 
 // ---------------------------------------------------------------------------
 // partition: one tile per ticket.  The tile's keys and payloads are copied
-// into shared memory with cp.async (coalesced, no registers), the keys are
-// ranked by digit (digits and ranks packed in registers), and the ranking is
-// written as a permutation perm[sorted position] = tile position.  The tile
-// is placed after its predecessors in the same bucket through a single-pass
-// decoupled look-back: every tile publishes its per-digit count (AGGREGATE)
-// as soon as it is ranked, and its inclusive prefix (INCLUSIVE) once known; a
-// tile sums its predecessors' cells back to the first INCLUSIVE one.  Finally
-// the tile is written in sorted order, so that the global writes of every
-// digit run are contiguous.
+// into shared memory with 16-byte cp.async (from the 16-byte boundary at or
+// below the tile's first element), the keys move to registers and are ranked
+// by digit (digits and ranks packed in registers), and the tile is staged in
+// shared memory in sorted order, in place: keys first, then payloads.  The
+// tile is placed after its predecessors in the same bucket through a
+// single-pass decoupled look-back: every tile publishes its per-digit count
+// (AGGREGATE) as soon as it is ranked, and its inclusive prefix (INCLUSIVE)
+// once known; a tile sums its predecessors' cells back to the first INCLUSIVE
+// one, reading kLookbackWindow cells per round.  Finally the staged tile is
+// written out in order, so that the global writes of every digit run are
+// contiguous.
 // Cell encoding: 0 = not ready, value+1 in bits 0..30, bit 31 = INCLUSIVE.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kInclusive = 0x80000000u;
+constexpr int kLookbackWindow = 8;
 
 template <int KB, int VB, bool STABLE>
 struct PartitionSmem {
     static constexpr int T = PartShape<KB>::kTile;
     typename RankSmemFor<STABLE>::T rank;
-    long long offs[kRadix];
+    int offs[kRadix];          // bucket-relative destination of digit d's run, minus its tile start
     uint32_t next_ticket;
-    alignas(16) unsigned char keys[T * KB];
-    alignas(16) unsigned char vals[VB ? T * VB : 16];
-    uint16_t perm[T];
+    alignas(16) unsigned char keys[T * KB + 16];
+    alignas(16) unsigned char vals[VB ? T * VB + 16 : 16];
 };
 
+// Issues cp.async copies of the 16-byte chunks that hold elements [0, len) of
+// src (EB-byte elements, src aligned to EB) into dst, starting from the chunk
+// boundary at or below src; returns the index of src[0] in dst.  Every chunk
+// read holds at least one element of the range.  dst holds len * EB + 16 bytes.
+template <int EB>
+__device__ __forceinline__ int stage_in(unsigned char *dst, const void *src, int len) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t a0 = a & ~(uintptr_t)15;
+    const uintptr_t a1 = (a + (uintptr_t)len * EB + 15) & ~(uintptr_t)15;
+    const int nchunk = (int)((a1 - a0) >> 4);
+    for (int c = threadIdx.x; c < nchunk; c += kThreads)
+        cp_async<16>(dst + 16 * c, reinterpret_cast<const void *>(a0 + 16 * (uintptr_t)c));
+    return (int)((a - a0) / EB);
+}
+
+// Sum of the counts of digit threadIdx.x over tiles first .. t-1 back to the
+// nearest INCLUSIVE cell (tile `first`, the bucket's first tile, publishes
+// INCLUSIVE at once).  A cell that stays 0 past the time limit sets
+// BINAR_ERR_DEVICE_TIMEOUT and ends the walk.
+__device__ __forceinline__ uint32_t lookback(const Ws &ws, const Params &p, uint32_t t,
+                                             uint32_t first) {
+    const int tid = threadIdx.x;
+    uint32_t excl = 0;
+    long long pt = (long long)t - 1;
+    for (;;) {
+        uint32_t x[kLookbackWindow];
+#pragma unroll
+        for (int i = 0; i < kLookbackWindow; i++)
+            x[i] = (pt - i >= (long long)first)
+                       ? ld_relaxed(ws.cells + (size_t)(pt - i) * kRadix + tid)
+                       : (kInclusive | 1u);
+#pragma unroll
+        for (int i = 0; i < kLookbackWindow; i++) {
+            if (x[i] == 0) {
+                const uint32_t *pc = ws.cells + (size_t)(pt - i) * kRadix + tid;
+                const unsigned long long t0 = globaltimer_ns();
+                while ((x[i] = ld_relaxed(pc)) == 0) {
+                    __nanosleep(32);
+                    if ((long long)(globaltimer_ns() - t0) > p.timeout_ns) {
+                        set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
+                        x[i] = kInclusive | 1u;
+                        break;
+                    }
+                }
+            }
+            excl += (x[i] & ~kInclusive) - 1;
+            if (x[i] & kInclusive) return excl;
+        }
+        pt -= kLookbackWindow;
+    }
+}
+
 template <int KB, int VB, bool STABLE>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, PartShape<KB>::kMinBlocks)
     k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
                 void *vals1) {
     using KT = KeyTraits<KB>;
@@ -788,6 +916,9 @@ __global__ void __launch_bounds__(kThreads, 3)
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const int tid = threadIdx.x;
+    if constexpr (STABLE) {
+        for (int i = tid & 31; i < kRadix; i += 32) s.rank.wmask[(tid >> 5) * kRadix + i] = 0;
+    }
     for (;;) {
         if (tid == 0) s.next_ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
         __syncthreads();
@@ -799,25 +930,24 @@ __global__ void __launch_bounds__(kThreads, 3)
         if (bk.flags & kSkip) continue;
         const uint32_t ti = t - bk.tile_start;
         const long long tb = bk.begin + (long long)ti * T;
-        const long long bend = bk.begin + (long long)bk.len;
-        const int tlen = (int)min((long long)T, bend - tb);
+        const int tlen = (int)min((long long)T, (long long)bk.begin + (long long)bk.len - tb);
         const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? keys1 : keys0) + tb;
         const V *vsrc = VB ? reinterpret_cast<const V *>(bk.buf ? vals1 : vals0) + tb : nullptr;
-        Raw *dst = reinterpret_cast<Raw *>(bk.buf ? keys0 : keys1);
-        V *vdst = VB ? reinterpret_cast<V *>(bk.buf ? vals0 : vals1) : nullptr;
+        Raw *dst = reinterpret_cast<Raw *>(bk.buf ? keys0 : keys1) + bk.begin;
+        V *vdst = VB ? reinterpret_cast<V *>(bk.buf ? vals0 : vals1) + bk.begin : nullptr;
 
-        for (int i = tid; i < tlen; i += kThreads) {
-            cp_async<KB>(&skeys[i], &src[i]);
-            if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
-        }
+        const int ks = stage_in<KB>(s.keys, src, tlen);
+        const int vs = VB ? stage_in<VB>(s.vals, vsrc, tlen) : 0;
         cp_async_wait_all();
         __syncthreads();
 
+        Raw k[ITEMS];
         Packed<ITEMS> pk;
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             const int i = striped(ITEMS, j);
-            pk.set_dig(j, i < tlen ? KT::digit(enc(skeys[i]), bk.pos) : 0u);
+            k[j] = skeys[ks + i];
+            pk.set_dig(j, i < tlen ? KT::digit(enc(k[j]), bk.pos) : 0u);
         }
         rank_tile<ITEMS>(pk, ITEMS, tlen, s.rank);
 
@@ -827,60 +957,46 @@ __global__ void __launch_bounds__(kThreads, 3)
         const bool hooked = (level == 0 && (int)t == p.skip_publish_tile);
         if (!hooked) st_relaxed(cell, (ti == 0 ? kInclusive : 0u) | (cnt + 1));
 
+        // stage the tile in sorted order, in place (its inputs are in registers)
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             const int i = striped(ITEMS, j);
             if (i < tlen) {
                 const uint32_t r = pk.rank(j);
-                if (r < (uint32_t)tlen) s.perm[r] = (uint16_t)i;
+                if (r < (uint32_t)tlen) skeys[r] = k[j];
                 else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
             }
         }
+        if (VB) {
+            V v[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) v[j] = svals[vs + striped(ITEMS, j)];
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                const uint32_t r = pk.rank(j);
+                if (striped(ITEMS, j) < tlen && r < (uint32_t)tlen) svals[r] = v[j];
+            }
+        }
 
-        // look-back over the bucket's earlier tiles (thread = digit)
         uint32_t excl = 0;
         if (ti > 0) {
-            uint32_t pt = t - 1;
-            for (;;) {
-                const uint32_t *pc = ws.cells + (size_t)pt * kRadix + tid;
-                uint32_t v = ld_relaxed(pc);
-                if (v == 0) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    while ((v = ld_relaxed(pc)) == 0) {
-                        __nanosleep(32);
-                        if ((long long)(globaltimer_ns() - t0) > p.timeout_ns) {
-                            set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
-                            v = kInclusive | 1u;
-                            break;
-                        }
-                    }
-                }
-                excl += (v & ~kInclusive) - 1;
-                if ((v & kInclusive) || pt == bk.tile_start) break;
-                pt--;
-            }
+            excl = lookback(ws, p, t, bk.tile_start);
             if (!hooked) st_relaxed(cell, kInclusive | (excl + cnt + 1));
         }
-        s.offs[tid] = bk.begin + (long long)prefix[(size_t)b * kRadix + tid] + excl -
-                      (long long)s.rank.dstart[tid];
+        s.offs[tid] = (int)(prefix[(size_t)b * kRadix + tid] + excl) - (int)s.rank.dstart[tid];
         __syncthreads();
 
         // write-out in sorted order: the digit runs are contiguous in memory
-#pragma unroll 8
+#pragma unroll 4
         for (int r = 0; r < ITEMS; r++) {
             const int i = r * kThreads + tid;
             if (i < tlen) {
-                int q = s.perm[i];
-                if (q >= tlen) {
-                    set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                    q = 0;
-                }
-                const Raw k = skeys[q];
-                const uint32_t d = KT::digit(enc(k), bk.pos);
-                const long long at = s.offs[d] + i;
-                if (at >= bk.begin && at < bend) {
-                    dst[at] = k;
-                    if (VB) vdst[at] = svals[q];
+                const Raw kk = skeys[i];
+                const uint32_t at = (uint32_t)(s.offs[KT::digit(enc(kk), bk.pos)] + i);
+                if (at < bk.len) {
+                    dst[at] = kk;
+                    if (VB) vdst[at] = svals[i];
                 } else {
                     set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
                 }
