@@ -15,7 +15,8 @@ namespace binar {
 template <int KB, int VB, bool STABLE>
 int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int level,
                      void *k0, void *k1, void *v0, void *v1) {
-    auto kfn = k_partition<KB, VB, STABLE>;
+    auto kfn = p.map == BINAR_MAP_UNSIGNED ? k_partition<KB, VB, STABLE, true>
+                                           : k_partition<KB, VB, STABLE, false>;
     const size_t smem = sizeof(PartitionSmem<KB, VB, STABLE>);
     int occ = kernel_ctas_per_sm((const void *)kfn, smem);
     if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;

@@ -896,7 +896,8 @@ __device__ __forceinline__ uint32_t lookback(const Ws &ws, const Params &p, uint
     }
 }
 
-template <int KB, int VB, bool STABLE>
+// IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
+template <int KB, int VB, bool STABLE, bool IDENT>
 __global__ void __launch_bounds__(kThreads, PartShape<KB>::kMinBlocks)
     k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
                 void *vals1) {
@@ -910,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB>::kMinBlocks)
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
-    const Encoder<KB> enc(p.map);
+    const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     const uint32_t *prefix = slot ? ws.hist[1] : ws.hist[0];
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
