@@ -1027,17 +1027,14 @@ constexpr int kFinishBits = 12;
 constexpr int kFinishBins = 1 << kFinishBits;
 constexpr int kFinishRun = 32;
 
-// 16-bit counters and run starts, two per word (counts and starts stay below
-// the job size, < 65536).
+// Split counters: 16-bit counts, two bins per word, in the first half of cs;
+// after the scan cs[d] = start of bin d | count of bin d << 16 (counts and
+// starts stay below the job size, < 65536).
 struct FinishFastSmem {
-    uint32_t cnt2[kFinishBins / 2];
-    uint32_t start2[kFinishBins / 2];
+    uint32_t cs[kFinishBins];
     uint32_t scratch[kWarps];
     uint32_t maxrun;
 };
-__device__ __forceinline__ uint32_t half16(const uint32_t *a, uint32_t d) {
-    return (a[d >> 1] >> ((d & 1) * 16)) & 0xffffu;
-}
 
 template <int KB, int VB, int IU>
 struct FinishSmem {
@@ -1124,7 +1121,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
     const int tid = threadIdx.x, lane = tid & 31;
     const int len = (int)job.len;
     FinishFastSmem &fs = s.u.fast;
-    for (int i = tid; i < kFinishBins / 2; i += kThreads) fs.cnt2[i] = 0;
+    for (int i = tid; i < kFinishBins / 2; i += kThreads) fs.cs[i] = 0;
     if (tid == 0) fs.maxrun = 0;
 
     // encode once, in registers; AND / OR of the job
@@ -1164,10 +1161,10 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
         uint32_t r = 0;
         if (__all_sync(0xffffffffu, valid && d == d0)) {
             uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&fs.cnt2[d0 >> 1], 32u << sh);
+            if (lane == 0) c = atomicAdd(&fs.cs[d0 >> 1], 32u << sh);
             r = ((__shfl_sync(0xffffffffu, c, 0) >> sh) & 0xffffu) + lane;
         } else if (valid) {
-            r = (atomicAdd(&fs.cnt2[d >> 1], 1u << sh) >> sh) & 0xffffu;
+            r = (atomicAdd(&fs.cs[d >> 1], 1u << sh) >> sh) & 0xffffu;
         }
         dr[k] = (d << 16) | r;
     }
@@ -1177,24 +1174,84 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
         uint32_t c[PW], sum = 0, mx = 0;
 #pragma unroll
         for (int q = 0; q < PW; q++) {
-            c[q] = fs.cnt2[tid * PW + q];
+            c[q] = fs.cs[tid * PW + q];
             const uint32_t lo = c[q] & 0xffffu, hi = c[q] >> 16;
             sum += lo + hi;
             mx = max(mx, max(lo, hi));
         }
         uint32_t total;
-        uint32_t run = block_exclusive_scan(sum, fs.scratch, &total);
+        uint32_t run = block_exclusive_scan(sum, fs.scratch, &total);   // all counts read
 #pragma unroll
         for (int q = 0; q < PW; q++) {
-            const uint32_t lo = run;
-            run += c[q] & 0xffffu;
-            fs.start2[tid * PW + q] = lo | (run << 16);
-            run += c[q] >> 16;
+            const uint32_t lo = c[q] & 0xffffu, hi = c[q] >> 16;
+            fs.cs[2 * (tid * PW + q)] = run | (lo << 16);
+            run += lo;
+            fs.cs[2 * (tid * PW + q) + 1] = run | (hi << 16);
+            run += hi;
         }
         if (mx > kFinishRun) atomicMax(&fs.maxrun, mx);
     }
     __syncthreads();
     if (fs.maxrun > (uint32_t)kFinishRun) return false;
+
+    if constexpr (KB == 4 || KB == 8) {
+        // Packed form: inside a run the keys agree on bits 0 .. f+11, so the
+        // stable order of a run is the order of P = (e << (f + 12)) | input
+        // position (only the position if the split reached the key's end).
+        // P fits the key's width when the position needs at most f + 12 bits.
+        const int sft = f + kFinishBits;
+        const int nidx = 32 - __clz((uint32_t)(len - 1) | 1u);
+        if (sft >= W || nidx <= sft) {
+            Bits *sp = reinterpret_cast<Bits *>(s.keys);
+            uint16_t *sd = s.perm;
+#pragma unroll
+            for (int k = 0; k < IU; k++) {
+                const int i = k * kThreads + tid;
+                if (i < len) {
+                    const uint32_t d = dr[k] >> 16;
+                    const uint32_t at = (fs.cs[d] & 0xffffu) + (dr[k] & 0xffffu);
+                    if (at < (uint32_t)len) {
+                        sp[at] = (sft < W ? (e[k] << sft) : (Bits)0) | (Bits)i;
+                        sd[at] = (uint16_t)d;
+                    } else {
+                        set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                    }
+                }
+            }
+            __syncthreads();
+            // the bits above f are the job's common prefix
+            const Bits pre = f ? (a & (KT::ones() << (W - f))) : (Bits)0;
+            const Bits imask = ((Bits)1 << nidx) - 1;
+#pragma unroll
+            for (int k = 0; k < IU; k++) {
+                const int x = k * kThreads + tid;
+                if (x < len) {
+                    const Bits px = sp[x];
+                    const uint32_t d = sd[x];
+                    const uint32_t bc = fs.cs[d];
+                    const int b0 = (int)(bc & 0xffffu), m = (int)(bc >> 16);
+                    int rank = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const Bits py = sp[min(b0 + t, len - 1)];
+                        rank += (t < m && py < px) ? 1 : 0;
+                    }
+                    for (int y = b0 + 4; y < b0 + m; y++) rank += sp[y] < px ? 1 : 0;
+                    uint32_t ix = (uint32_t)(px & imask);
+                    if (ix >= (uint32_t)len) {
+                        set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                        ix = 0;
+                    }
+                    const Bits ex = pre | (sft < W ? (((Bits)d << (W - sft)) | (px >> sft))
+                                                   : ((Bits)d >> (sft - W)));
+                    const int at = min(b0 + rank, len - 1);
+                    dst[at] = dec(ex);
+                    if (VB) vdst[at] = svals[ix];
+                }
+            }
+            return true;
+        }
+    }
 
     // place the encoded keys in split order (over the raw keys, all read), with
     // their input positions
@@ -1203,7 +1260,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
     for (int k = 0; k < IU; k++) {
         const int i = k * kThreads + tid;
         if (i < len) {
-            const uint32_t at = half16(fs.start2, dr[k] >> 16) + (dr[k] & 0xffffu);
+            const uint32_t at = (fs.cs[dr[k] >> 16] & 0xffffu) + (dr[k] & 0xffffu);
             if (at < (uint32_t)len) {
                 senc[at] = e[k];
                 s.perm[at] = (uint16_t)i;
@@ -1223,7 +1280,8 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
             const Bits ex = senc[x];
             const uint32_t ix = s.perm[x];
             const uint32_t d = KT::bits_at(ex, f, kFinishBits);
-            const int b0 = (int)half16(fs.start2, d), m = (int)half16(fs.cnt2, d);
+            const uint32_t bc = fs.cs[d];
+            const int b0 = (int)(bc & 0xffffu), m = (int)(bc >> 16);
             int rank = 0;
 #pragma unroll
             for (int t = 0; t < 4; t++) {
