@@ -1045,8 +1045,8 @@ struct FinishSmem {
     uint4 sand[kWarps], sor[kWarps];
     uint32_t next_ticket;
     Job next_job;
-    alignas(16) unsigned char keys[T * KB];
-    alignas(16) unsigned char vals[VB ? T * VB : 16];
+    alignas(16) unsigned char keys[T * KB + 16];
+    alignas(16) unsigned char vals[VB ? T * VB + 16 : 16];
     uint16_t perm[T];
 };
 
@@ -1109,7 +1109,8 @@ __device__ __forceinline__ void block_and_or(typename KeyTraits<KB>::Bits &a,
 template <int KB, int VB, int IU>
 __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws &ws,
                                             const Encoder<KB> &enc, const Decoder<KB> &dec,
-                                            const Job &job, typename KeyTraits<KB>::Raw *dst,
+                                            const Job &job, int ks, int vs,
+                                            typename KeyTraits<KB>::Raw *dst,
                                             typename ValTraits<VB>::T *vdst) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
@@ -1131,7 +1132,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
     for (int k = 0; k < IU; k++) {
         const int i = k * kThreads + tid;
         if (i < len) {
-            e[k] = enc(skeys[i]);
+            e[k] = enc(skeys[ks + i]);
             a = a & e[k];
             o = o | e[k];
         }
@@ -1142,8 +1143,8 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
         // all keys equal: already in order
         if (job.buf == 1) {
             for (int i = tid; i < len; i += kThreads) {
-                dst[i] = skeys[i];
-                if (VB) vdst[i] = svals[i];
+                dst[i] = skeys[ks + i];
+                if (VB) vdst[i] = svals[vs + i];
             }
         }
         return true;
@@ -1246,7 +1247,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
                                                    : ((Bits)d >> (sft - W)));
                     const int at = min(b0 + rank, len - 1);
                     dst[at] = dec(ex);
-                    if (VB) vdst[at] = svals[ix];
+                    if (VB) vdst[at] = svals[vs + ix];
                 }
             }
             return true;
@@ -1297,7 +1298,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
             }
             const int at = min(b0 + rank, len - 1);
             dst[at] = dec(ex);
-            if (VB) vdst[at] = svals[ix];
+            if (VB) vdst[at] = svals[vs + ix];
         }
     }
     return true;
@@ -1341,11 +1342,10 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
         const V *vsrc = VB ? reinterpret_cast<const V *>(job.buf ? vals1 : vals0) + job.begin : nullptr;
         V *vdst = VB ? reinterpret_cast<V *>(vals0) + job.begin : nullptr;
         const bool trivial = job.pos >= W || len <= 1 || len > kThreads * IU;
+        int ks = 0, vs = 0;
         if (!trivial) {
-            for (int i = tid; i < len; i += kThreads) {
-                cp_async<KB>(&skeys[i], &src[i]);
-                if (VB) cp_async<VB ? VB : 4>(&svals[i], &vsrc[i]);
-            }
+            ks = stage_in<KB>(s.keys, src, len);
+            if (VB) vs = stage_in<VB>(s.vals, vsrc, len);
         }
         if (tid == 0) {   // the next job, while this one's data arrives
             const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
@@ -1365,7 +1365,7 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
         }
         cp_async_wait_all();
         __syncthreads();
-        if (!finish_fast<KB, VB, IU>(s, ws, enc, dec, job, dst, vdst) && tid == 0) {
+        if (!finish_fast<KB, VB, IU>(s, ws, enc, dec, job, ks, vs, dst, vdst) && tid == 0) {
             // runs too long for the fast path: the job goes to the LSD path
             const uint32_t ji = atomicAdd(&ws.ctr->njobs2, 1u);
             if (ji < ws.jcap) ws.jobs2[ji] = job;
