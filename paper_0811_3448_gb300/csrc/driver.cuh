@@ -75,7 +75,7 @@ int run_call_vb(const Call &c) {
         if ((rc = launch("prep", 0, c.stream, [&] { k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, 0); })))
             return rc;
         {
-            auto hfn = k_hist<KB>;
+            auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
             const int occ = kernel_ctas_per_sm((const void *)hfn, 0);
             if ((rc = launch("hist", 0, c.stream, [&] {
                      hfn<<<sms * (occ > 0 ? occ : 1), kThreads, 0, c.stream>>>(ws, p, 0, 0);
@@ -110,7 +110,7 @@ int run_call_vb(const Call &c) {
             return rc;
     }
     if (seg || c.n > c.cutoff) {
-        auto hfn = k_hist<KB>;
+        auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
         const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
         const int hgrid = sms * (hocc > 0 ? hocc : 1);
         for (int l = 0; l < L; l++) {

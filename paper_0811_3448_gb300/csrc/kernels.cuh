@@ -494,17 +494,32 @@ static __global__ void k_prep(Ws ws, int slot) {
 // ---------------------------------------------------------------------------
 constexpr int kHistGroup = 8;
 
+// The 16 / KB keys held in one 16-byte chunk (little-endian words).
 template <int KB>
+__device__ __forceinline__ void unpack_chunk(const uint4 &v, typename KeyTraits<KB>::Raw *r) {
+    if constexpr (KB == 4) {
+        r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w;
+    } else if constexpr (KB == 8) {
+        r[0] = ((uint64_t)v.y << 32) | v.x;
+        r[1] = ((uint64_t)v.w << 32) | v.z;
+    } else {
+        r[0] = v;
+    }
+}
+
+// IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
+template <int KB, bool IDENT>
 __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
     constexpr int T = PartShape<KB>::kTile;
+    constexpr int PER = 16 / KB;
     __shared__ uint32_t sh[kWarps][kRadix];
     __shared__ uint4 sand[kWarps], sor[kWarps];
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
-    const Encoder<KB> enc(p.map);
+    const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     uint32_t *hist = slot ? ws.hist[1] : ws.hist[0];
     uint4 *andor = slot ? ws.andor[1] : ws.andor[0];
@@ -579,12 +594,27 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
             const long long tb = bk.begin + (long long)(t - bk.tile_start) * T;
             const int tlen = (int)min((long long)T, bk.begin + (long long)bk.len - tb);
             const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
+            // 16-byte chunks from the boundary at or below src (every chunk holds
+            // at least one key of the tile); keys outside the tile are skipped
+            const uintptr_t a1 = reinterpret_cast<uintptr_t>(src);
+            const uintptr_t a0 = a1 & ~(uintptr_t)15;
+            const int shift = (int)((a1 - a0) / KB);
+            const int nchunk = (int)((((a1 + (uintptr_t)tlen * KB + 15) & ~(uintptr_t)15) - a0) >> 4);
+            const uint4 *c4 = reinterpret_cast<const uint4 *>(a0);
 #pragma unroll 4
-            for (int i = tid; i < tlen; i += kThreads) {
-                const Bits x = enc(src[i]);
-                a = a & x;
-                o = o | x;
-                atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+            for (int c = tid; c < nchunk; c += kThreads) {
+                Raw r[PER];
+                unpack_chunk<KB>(__ldg(c4 + c), r);
+#pragma unroll
+                for (int e = 0; e < PER; e++) {
+                    const int idx = c * PER + e - shift;
+                    if (idx >= 0 && idx < tlen) {
+                        const Bits x = enc(r[e]);
+                        a = a & x;
+                        o = o | x;
+                        atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                    }
+                }
             }
         }
     }
