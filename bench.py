@@ -168,6 +168,23 @@ def cpu_baseline(n_sample: int, dist: str):
                       f"(leading-bit split, one thread per group), {dt:.2f} s wall"}
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it); ms itself without a
+    process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n: int, world: int, ms_max: float) -> float:
+    """Whole-job GKeys/s: every rank sorts its own n keys; the job takes the
+    slowest rank's time."""
+    return world * n / (ms_max * 1e-3) / 1e9
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, each step a bounded sample of the workload."""
     world, rank, _ = dist_env()
@@ -352,12 +369,8 @@ def run_binar(args):
     sampler.stop()
     binding.check_status(ws)
     ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * n / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(ms, dist, dev)
+    value = replica_throughput(n, world, ms_max)
     valid = check_sorted_stable(keys, vals, keys0)
 
     # roofline of the first partition pass (the whole array, one read + one write)

@@ -48,8 +48,9 @@ def _store_cache(cache: dict) -> None:
         pass   # a read-only home is not an error: the result is just not kept
 
 
-def shape_key(n: int, key_bytes: int, val_bytes: int, num_segments: int = 0) -> str:
-    dev = torch.cuda.get_device_name()
+def shape_key(n: int, key_bytes: int, val_bytes: int, num_segments: int = 0,
+              device_name: str = None) -> str:
+    dev = torch.cuda.get_device_name() if device_name is None else device_name
     seg_class = 0 if num_segments <= 1 else int(math.log2(num_segments)) + 1
     return f"{dev}|k{key_bytes}|v{val_bytes}|n2^{max(0, int(math.log2(max(n, 1))))}|s{seg_class}"
 
