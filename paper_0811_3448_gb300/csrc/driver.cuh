@@ -30,7 +30,9 @@ template <int KB, int VB, int CLS>
 int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1, void *v0,
                         void *v1) {
     constexpr int IU = FinishClasses<KB>::iu(CLS);
-    auto ffn = k_finish<KB, VB, CLS>;
+    // the identity key map is compiled separately for 4- and 8-byte keys
+    auto ffn = (KB != 16 && c.map == BINAR_MAP_UNSIGNED) ? k_finish<KB, VB, CLS, KB != 16>
+                                                         : k_finish<KB, VB, CLS, false>;
     const size_t smem = sizeof(FinishSmem<KB, VB, IU>);
     const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
     return launch("finish", CLS, c.stream, [&] {
@@ -149,16 +151,6 @@ int run_call_vb(const Call &c) {
     return launch("copy", -1, c.stream, [&] {
         k_copy<KB, VB><<<small_grid, kThreads, 0, c.stream>>>(ws, k0, k1, v0, v1);
     });
-}
-
-template <int KB>
-int run_call(const Call &c) {
-    switch (c.vb) {
-    case 0: return run_call_vb<KB, 0>(c);
-    case 4: return run_call_vb<KB, 4>(c);
-    case 8: return run_call_vb<KB, 8>(c);
-    default: return BINAR_ERR_UNSUPPORTED;
-    }
 }
 
 }  // namespace binar

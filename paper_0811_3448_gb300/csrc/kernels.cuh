@@ -1334,7 +1334,8 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
     return true;
 }
 
-template <int KB, int VB, int CLS>
+// IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
+template <int KB, int VB, int CLS, bool IDENT>
 __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2)
     k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
@@ -1347,8 +1348,8 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
-    const Encoder<KB> enc(p.map);
-    const Decoder<KB> dec(p.map);
+    const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
+    const Decoder<KB> dec(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     uint32_t base = 0;
     for (int c = 0; c < CLS; c++) base += ws.ctr->class_count[c];
     const uint32_t count = ws.ctr->class_count[CLS];

@@ -1,6 +1,19 @@
-// Kernels and level loop for 16-byte keys (byte strings, 128-bit integers).
-#include "driver.cuh"
+// Dispatch by payload width for 16-byte keys (byte strings, 128-bit integers).  The kernels and level loop
+// of each payload width compile in their own translation unit
+// (keys16_v0.cu, keys16_v4.cu, keys16_v8.cu) so that they build in parallel.
+#include "layout.cuh"
 
 namespace binar {
-int run_call_k16(const Call &c) { return run_call<16>(c); }
+int run_call_k16_v0(const Call &c);
+int run_call_k16_v4(const Call &c);
+int run_call_k16_v8(const Call &c);
+
+int run_call_k16(const Call &c) {
+    switch (c.vb) {
+    case 0: return run_call_k16_v0(c);
+    case 4: return run_call_k16_v4(c);
+    case 8: return run_call_k16_v8(c);
+    default: return BINAR_ERR_UNSUPPORTED;
+    }
+}
 }  // namespace binar

@@ -1,0 +1,6 @@
+// Kernels and level loop for 4-byte keys (uint32, int32, float32) with 4-byte payloads.
+#include "driver.cuh"
+
+namespace binar {
+int run_call_k4_v4(const Call &c) { return run_call_vb<4, 4>(c); }
+}  // namespace binar
