@@ -36,13 +36,21 @@ FALLBACK_HBM_GBS = 6800.0
 WORKLOAD = "256M uint32 keys + uint32 index payload, uniform, stable in-place sort"
 
 
+def workload_name(n: int, key: str, dist: str) -> str:
+    kname = "uint64" if key == "u64" else "uint32"
+    return f"{n >> 20}M {kname} keys + uint32 index payload, {dist}, stable in-place sort"
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["binar", "reference"], default="binar")
-    ap.add_argument("--n", type=int, default=256 << 20)
+    ap.add_argument("--n", type=int, default=0,
+                    help="keys (default: 256M for uint32 keys, 128M for uint64 keys)")
+    ap.add_argument("--key", choices=["u32", "u64"], default="u32",
+                    help="pairs workload key type (payload: uint32 original index)")
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -54,7 +62,10 @@ def parse_args():
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
     ap.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.n <= 0:
+        args.n = (128 << 20) if (args.key == "u64" and args.workload == "pairs") else (256 << 20)
+    return args
 
 
 def dist_env():
@@ -152,19 +163,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-def cpu_baseline(n_sample: int, dist: str):
+def cpu_baseline(n_sample: int, dist: str, kdt=np.uint32):
     """The oracle's parallel binar sort on the host cores, on a bounded sample."""
     import oracle
     from paper_0811_3448_gb300 import inputs
     cores = os.cpu_count() or 1
     log2g = max(0, int(math.floor(math.log2(cores))))
-    keys = inputs.config2_keys(n_sample, np.uint32, dist)
+    keys = inputs.config2_keys(n_sample, kdt, dist)
     vals = inputs.index_payload(n_sample)
     t0 = time.perf_counter()
     oracle.binar_sort_parallel(keys, vals, log2_groups=log2g)
     dt = time.perf_counter() - t0
     return {"value": n_sample / dt / 1e9, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
-            "sample": f"{n_sample} uint32 keys + uint32 payload ({dist}), parallel binar sort "
+            "sample": f"{n_sample} {np.dtype(kdt).name} keys + uint32 payload ({dist}), parallel binar sort "
                       f"(leading-bit split, one thread per group), {dt:.2f} s wall"}
 
 
@@ -187,6 +198,7 @@ def replica_throughput(n: int, world: int, ms_max: float) -> float:
 
 def run_reference(args):
     """Reference arm: the CPU oracle, each step a bounded sample of the workload."""
+    kdt = np.uint64 if args.key == "u64" else np.uint32
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -196,14 +208,14 @@ def run_reference(args):
     log2g = max(0, int(math.floor(math.log2(cores))))
     # calibrate the sample so that warmup + steps take about 90 s
     probe = 1 << 20
-    k = inputs.config2_keys(probe, np.uint32, args.dist)
+    k = inputs.config2_keys(probe, kdt, args.dist)
     v = inputs.index_payload(probe)
     t0 = time.perf_counter()
     oracle.binar_sort_parallel(k, v, log2_groups=log2g)
     rate = probe / max(time.perf_counter() - t0, 1e-6)
     per_step = 90.0 / max(1, args.steps + args.warmup)
     n = int(min(args.n, max(1 << 18, rate * per_step)))
-    keys = inputs.config2_keys(n, np.uint32, args.dist)
+    keys = inputs.config2_keys(n, kdt, args.dist)
     vals = inputs.index_payload(n)
     times = []
     for i in range(args.warmup + args.steps):
@@ -217,8 +229,8 @@ def run_reference(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "u32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": args.n, "sample_n": n, "dist": args.dist,
+           "dtype": args.key, "data": "synthetic",
+           "config": {"workload": workload_name(args.n, args.key, args.dist), "n": args.n, "sample_n": n, "dist": args.dist,
                       "parallelism": "replicas"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
                             "sample": f"{n} keys per step (bounded sample of the {args.n}-key "
@@ -231,10 +243,16 @@ def run_reference(args):
 def check_sorted_stable(tk, tv, orig_keys_dev):
     """Sorted, a permutation of the input, and stable (payload = index)."""
     import torch
-    k = tk.to(torch.int64)
+    if tk.dtype == torch.uint64:   # compare as unsigned: flip the sign bit of the int64 view
+        flip = torch.tensor(-(2 ** 63), dtype=torch.int64, device=tk.device)
+        k = tk.view(torch.int64) ^ flip
+        orig = orig_keys_dev.view(torch.int64) ^ flip
+    else:
+        k = tk.to(torch.int64)
+        orig = orig_keys_dev.to(torch.int64)
     v = tv.to(torch.int64)
     ok = bool((k[1:] >= k[:-1]).all())
-    ok &= bool((orig_keys_dev.to(torch.int64)[v] == k).all())
+    ok &= bool((orig[v] == k).all())
     ok &= bool((torch.bincount(v, minlength=k.shape[0]) == 1).all())
     eq = k[1:] == k[:-1]
     ok &= bool((v[1:][eq] > v[:-1][eq]).all())
@@ -252,6 +270,7 @@ def run_e2e(args, binding, torch, dev, keys_h, vals_h, ws, keys, vals, world):
     sets keep both link directions busy).  The serial
     form (copy in, sort, copy out, one step at a time) is reported beside it."""
     n = keys_h.shape[0]
+    rec = keys_h.itemsize + vals_h.itemsize      # bytes per record each way
     hk = torch.from_numpy(keys_h).pin_memory()
     hv = torch.from_numpy(vals_h).pin_memory()
     ok_k = torch.empty_like(hk).pin_memory()
@@ -316,7 +335,7 @@ def run_e2e(args, binding, torch, dev, keys_h, vals_h, ws, keys, vals, world):
     binding.check_status(ws)
     ser = statistics.mean(serial)
     return {"value": world * n / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": ms,
+            "h2d_bytes_per_step": rec * n, "d2h_bytes_per_step": rec * n, "ms_per_step": ms,
             "steps": steps, "form": "streamed: step i's copy out overlaps later steps' copy in "
                                     "and sort (three device buffer sets)",
             "serial": {"value": world * n / (ser * 1e-3) / 1e9, "ms_per_step": ser}}
@@ -337,14 +356,16 @@ def run_binar(args):
     binding.load()
     dev = torch.device("cuda", local)
     n = args.n
+    kb = 8 if args.key == "u64" else 4
+    kdt = np.uint64 if kb == 8 else np.uint32
 
-    keys_h = inputs.config2_keys(n, np.uint32, args.dist)
+    keys_h = inputs.config2_keys(n, kdt, args.dist)
     vals_h = inputs.index_payload(n)
     keys0 = torch.from_numpy(keys_h).to(dev)
     vals0 = torch.from_numpy(vals_h).to(dev)
     keys = torch.empty_like(keys0)
     vals = torch.empty_like(vals0)
-    ws = binding.workspace(n, 4, 4, device=dev)
+    ws = binding.workspace(n, kb, 4, device=dev)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -393,7 +414,7 @@ def run_binar(args):
     roofline = None
     if part:
         per_launch_ms = part[1] / part[0]
-        alg_bytes = 2 * (4 + 4) * n
+        alg_bytes = 2 * (kb + 4) * n
         achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": "partition[0]", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -413,8 +434,9 @@ def run_binar(args):
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": n, "key": "uint32", "payload": "uint32",
+           "scaling": "weak", "vs_baseline": None, "dtype": args.key, "data": "synthetic",
+           "config": {"workload": workload_name(n, args.key, args.dist), "n": n,
+                      "key": "uint64" if kb == 8 else "uint32", "payload": "uint32",
                       "dist": args.dist, "parallelism": f"replicas x{world}",
                       "l2": "2 GiB inputs (> 129 MB L2), restored from a pristine copy "
                             "before every timed sort"},
@@ -422,7 +444,7 @@ def run_binar(args):
            "clocks": sampler.summary(), "validated": valid, "dominant_kernel": dominant,
            "kernels": kernels, "wall_s_timed_loop": wall}
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(32 << 20, args.dist)
+        out["cpu_baseline"] = cpu_baseline(32 << 20, args.dist, kdt)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
