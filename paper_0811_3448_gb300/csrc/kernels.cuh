@@ -646,6 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     __shared__ Job sjobs[kRadix];            // this parent's finisher jobs
     __shared__ CopyJob scopies[kRadix];      // and copy jobs (tile_start relative)
     __shared__ uint32_t snjobs, sncopies, scopy_tiles;
+    __shared__ unsigned long long scopy_acc;
     __shared__ uint32_t sjob_base;
     __shared__ unsigned long long scopy_base;
     if (has_error(ws.ctr)) return;
@@ -739,16 +740,24 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 ws.list[next][bi] = nbk;
             }
         }
-        // small and finished children: runs, by one thread in digit order, into
-        // shared lists that are then reserved and written by the whole CTA
+        // small and finished children: runs of small children become merged
+        // jobs.  Each warp walks one aligned group of 32 digits (lane 0, digit
+        // order) and a run never crosses a group, so the keys of a merged job
+        // share the top 3 bits of their digit and its 12-bit split still sees
+        // at least 7 bits below the digit.  Jobs and copy jobs go to shared
+        // lists (slots by shared atomics; a copy job's slot and tile offset
+        // come from one 64-bit atomic, so both grow together), then the whole
+        // CTA reserves and writes them.
         if (tid == 0) {
             snjobs = 0;
-            sncopies = 0;
-            scopy_tiles = 0;
+            scopy_acc = 0ull;
+        }
+        __syncthreads();
+        if ((tid & 31) == 0) {
             const uint32_t C = (uint32_t)p.cutoff;
             const uint32_t own = C / 8;       // a child this large is a job of its own
             long long run_begin = -1;
-            uint32_t run_len = 0, run_children = 0, run_child_pos = 0;
+            uint32_t run_len = 0, run_children = 0;
             auto emit = [&](long long begin, uint32_t len, uint32_t children) {
                 if (len == 0) return;
                 int jpos = terminal ? W : (children == 1 ? cpos : bk.pos);
@@ -760,10 +769,12 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 j.pos = (uint16_t)jpos;
                 j.buf = (uint8_t)cbuf;
                 j.pad = 0;
-                sjobs[snjobs++] = j;
+                const uint32_t slot = atomicAdd(&snjobs, 1u);
+                if (slot < (uint32_t)kRadix) sjobs[slot] = j;
+                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
             };
-            (void)run_child_pos;
-            for (int d = 0; d < kRadix; d++) {
+            const int d0 = (tid >> 5) * 32;
+            for (int d = d0; d < d0 + 32; d++) {
                 const uint32_t c = scount[d];
                 if (c == 0) continue;
                 const long long cb = bk.begin + sexcl[d];
@@ -773,12 +784,16 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                     emit(run_begin, run_len, run_children);
                     run_begin = -1; run_len = 0; run_children = 0;
                     if (cbuf == 1) {
+                        const uint32_t tiles = (c + T - 1) / T;
+                        const unsigned long long got =
+                            atomicAdd(&scopy_acc, ((unsigned long long)tiles << 32) | 1ull);
+                        const uint32_t slot = (uint32_t)got;
                         CopyJob cj;
                         cj.begin = cb;
                         cj.len = c;
-                        cj.tile_start = scopy_tiles;
-                        scopies[sncopies++] = cj;
-                        scopy_tiles += (c + T - 1) / T;
+                        cj.tile_start = (uint32_t)(got >> 32);
+                        if (slot < (uint32_t)kRadix) scopies[slot] = cj;
+                        else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
                     }
                     continue;
                 }
@@ -804,6 +819,11 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 }
             }
             emit(run_begin, run_len, run_children);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sncopies = (uint32_t)scopy_acc;
+            scopy_tiles = (uint32_t)(scopy_acc >> 32);
             sjob_base = snjobs ? atomicAdd(&ws.ctr->njobs, snjobs) : 0u;
             scopy_base = sncopies ? atomicAdd(&ws.ctr->copy_alloc,
                                               ((unsigned long long)scopy_tiles << 32) | sncopies)

@@ -66,7 +66,10 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     const long long T = tile_for(kb), lv = levels_for(kb);
     const long long m = n / (kMinCutoff + 1) + segs + 2;
     const long long t = n / T + m + 2;
-    long long j = lv * (19 * (n / kMinCutoff) + 2 * m) + segs + 2;
+    // jobs of a level: own jobs (>= C/8 keys) and merged runs (two adjacent
+    // runs hold > C keys) give 19n/C; every parent adds at most 2 around its
+    // large children and 8 at its digit-group boundaries
+    long long j = lv * (19 * (n / kMinCutoff) + 10 * m) + segs + 2;
     if (j > n + 2) j = n + 2;
     const long long c = lv * (n / kMinCutoff + m) + 2;
     L.mcap = (uint32_t)m;
