@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
+    ap.add_argument("--span-log2", type=int, default=16,
+                    help="serve: request sizes floor(2^(10 + span U)) keys (16: 1K..64M)")
     ap.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
     args = ap.parse_args()
     if args.n <= 0:

@@ -7,9 +7,10 @@ Structure (one host thread, CUDA streams for overlap):
   ``budget_bytes`` is carved first-fit into 256-byte aligned blocks; a batch
   holds one block (its keys, payloads, offsets and workspace) from launch
   until its completion event has fired.  Admission is exactly "the block fits".
-* :class:`Scheduler` -- host logic only.  Requests wait in one FIFO.  When a
-  stream slot is free, the oldest request picks the class (key type, payload or
-  not); every queued request of that class joins the batch, in arrival order,
+* :class:`Scheduler` -- host logic only.  Requests wait in arrival order (one
+  deque per class).  When a stream slot is free, the oldest request picks the
+  class (key type, payload or not); queued requests of that class join the
+  batch, in arrival order,
   while the batch stays under ``max_batch_keys`` / ``max_batch_requests`` and
   its block fits the arena's largest free range.  If the oldest request does
   not fit, nothing launches until memory frees (no overtaking, so no request
@@ -29,6 +30,7 @@ arrival time (both on the host's monotonic clock).
 from __future__ import annotations
 
 import bisect
+import collections
 import dataclasses
 import math
 import os
@@ -94,6 +96,7 @@ class Request:
     has_payload: bool        # uint32 payload = index within the request
     seed: int                # SplitMix64 seed of the request's keys
     arrival_s: float = 0.0
+    _seq: int = -1           # submission number (set by the scheduler)
     status: str = "new"      # queued, running, done, rejected, failed
     t_launch: float = math.nan
     t_done: float = math.nan
@@ -151,7 +154,12 @@ class Batch:
 
 
 class Scheduler:
-    """Admission and batch formation (host logic only, no device calls)."""
+    """Admission and batch formation (host logic only, no device calls).
+
+    Queued requests wait in one deque per class, in arrival order; the oldest
+    request overall (smallest submission number) picks the class of the next
+    batch.  Forming a batch costs O(classes + batch size), however long the
+    backlog."""
 
     def __init__(self, arena: Arena, ws_bytes, max_batch_keys: int = 256 << 20,
                  max_batch_requests: int = 4096):
@@ -159,8 +167,19 @@ class Scheduler:
         self.ws_bytes = ws_bytes
         self.max_batch_keys = max_batch_keys
         self.max_batch_requests = max_batch_requests
-        self.queue: List[Request] = []
+        self.queues = {}
         self.rejected: List[Request] = []
+        self._seq = 0
+        self._queued = 0
+
+    @property
+    def queued(self) -> int:
+        return self._queued
+
+    @property
+    def queue(self) -> List[Request]:
+        """All queued requests in submission order (for inspection)."""
+        return sorted((r for q in self.queues.values() for r in q), key=lambda r: r._seq)
 
     def submit(self, r: Request) -> bool:
         if block_layout([r.n], r.key_bytes, r.val_bytes, self.ws_bytes).total > self.arena.capacity:
@@ -169,36 +188,37 @@ class Scheduler:
             self.rejected.append(r)
             return False
         r.status = "queued"
-        self.queue.append(r)
+        r._seq = self._seq
+        self._seq += 1
+        self.queues.setdefault(r.cls, collections.deque()).append(r)
+        self._queued += 1
         return True
 
     def next_batch(self) -> Optional[Batch]:
-        if not self.queue:
+        if self._queued == 0:
             return None
-        head = self.queue[0]
+        q = min((q for q in self.queues.values() if q), key=lambda q: q[0]._seq)
+        head = q[0]
         kb, vb = head.key_bytes, head.val_bytes
         room = self.arena.largest_free()
-        chosen, sizes, layout, total = [], [], None, 0
-        for r in self.queue:
-            if r.cls != head.cls:
-                continue
-            if len(chosen) >= self.max_batch_requests:
+        sizes, layout, total = [], None, 0
+        for r in q:
+            if len(sizes) >= self.max_batch_requests:
                 break
-            if chosen and total + r.n > self.max_batch_keys:
+            if sizes and total + r.n > self.max_batch_keys:
                 break
             trial = block_layout(sizes + [r.n], kb, vb, self.ws_bytes)
             if trial.total > room:
                 break
-            chosen.append(r)
             sizes.append(r.n)
             total += r.n
             layout = trial
-        if not chosen:
+        if not sizes:
             return None          # the oldest request waits for memory
         off = self.arena.alloc(layout.total)
         assert off is not None
-        picked = set(id(r) for r in chosen)
-        self.queue = [r for r in self.queue if id(r) not in picked]
+        chosen = [q.popleft() for _ in range(len(sizes))]
+        self._queued -= len(chosen)
         starts = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64).tolist()
         return Batch(head.cls, chosen, layout, off, starts)
 
@@ -315,7 +335,7 @@ class Server:
         reqs = sorted(requests, key=lambda r: r.arrival_s)
         t0 = time.perf_counter()
         i = 0
-        while i < len(reqs) or self.sched.queue or self.inflight:
+        while i < len(reqs) or self.sched.queued or self.inflight:
             now = time.perf_counter() - t0
             if now > max_wall_s:
                 raise RuntimeError("serving run exceeded its wall-clock limit")
@@ -336,7 +356,7 @@ class Server:
                 progressed = True
             if not progressed:
                 wait = 50e-6
-                if not self.inflight and not self.sched.queue and i < len(reqs):
+                if not self.inflight and not self.sched.queued and i < len(reqs):
                     wait = max(0.0, min(reqs[i].arrival_s - now, 0.01))
                 time.sleep(wait)
         return self.stats(reqs)
@@ -408,7 +428,8 @@ def bench_main(args) -> Optional[dict]:
     duration = getattr(args, "duration", 60.0)
     budget = int(getattr(args, "budget_gb", 40) * (1 << 30))
     slots = getattr(args, "slots", 4)
-    mix = inputs.config5_requests(rate_hz=rate, duration_s=duration)
+    span = getattr(args, "span_log2", 16)
+    mix = inputs.config5_requests(rate_hz=rate, duration_s=duration, span_log2=span)
     warm_up()
     torch.cuda.synchronize()
     out = {}
@@ -438,7 +459,7 @@ def bench_main(args) -> Optional[dict]:
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32/u64/f32", "data": "synthetic",
             "config": {"workload": f"serving: Poisson arrivals {rate:g}/s for {duration:g} s, "
-                                   "sizes floor(2^(10+16U)), key type uniform over "
+                                   f"sizes floor(2^(10+{span}U)), key type uniform over "
                                    "{uint32, uint64, float32}, uint32 payload with p=1/2, "
                                    f"{budget >> 30} GiB budget, {slots} stream slots",
                        "requests": len(mix)},

@@ -160,7 +160,7 @@ def test_simulated_run_drains_without_deadlock():
     a = Arena(budget)
     s = Scheduler(a, fake_ws, max_batch_keys=1 << 21)
     slots, inflight, t, i = 3, [], 0.0, 0
-    while i < len(reqs) or s.queue or inflight:
+    while i < len(reqs) or s.queued or inflight:
         nxt = [reqs[i].arrival_s] if i < len(reqs) else []
         nxt += [d for d, _ in inflight]
         t = max(t, min(nxt))
@@ -178,3 +178,20 @@ def test_simulated_run_drains_without_deadlock():
             inflight.append((t + 1e-9 * b.layout.n + 5e-6, b))
     assert all(r.status == "done" for r in reqs)
     assert a.used == 0 and a.peak <= budget
+
+
+def test_long_backlog_batches_in_constant_time_per_request():
+    """A backlog of 200,000 queued requests is drained one request per batch
+    without quadratic work (the plain form under overload)."""
+    import time
+    a = Arena(1 << 40)
+    s = Scheduler(a, fake_ws, max_batch_requests=1)
+    for i in range(200_000):
+        s.submit(_req(i, 1000, ("u32", "u64", "f32")[i % 3], bool(i & 1)))
+    t0 = time.perf_counter()
+    order = []
+    while (b := s.next_batch()) is not None:
+        order.append(b.requests[0].rid)
+        s.release(b)
+    assert order == list(range(200_000))           # oldest first across classes
+    assert time.perf_counter() - t0 < 30.0
