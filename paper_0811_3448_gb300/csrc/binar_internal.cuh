@@ -49,14 +49,24 @@ struct Job {
 };
 static_assert(sizeof(Job) == 16, "Job layout");
 
-// A finished bucket larger than the finisher cutoff that sits in the
-// workspace arrays and must be copied back to the caller's arrays.
+// A finished bucket larger than the finisher cutoff that must still be moved:
+// copied back from the workspace arrays to the caller's, or (kCopyReverse)
+// reversed -- strictly decreasing keys -- into the caller's arrays, in place
+// when it already sits there (kCopyInPlace).  The flags ride in the top bits
+// of `begin` (key indices stay below 2^61).
 struct CopyJob {
     long long begin;
     uint32_t len;
     uint32_t tile_start;
 };
 static_assert(sizeof(CopyJob) == 16, "CopyJob layout");
+constexpr long long kCopyReverse = 1LL << 62;
+constexpr long long kCopyInPlace = 1LL << 61;
+constexpr long long kCopyBeginMask = (1LL << 61) - 1;
+
+// Order flags of a bucket's adjacent key pairs (encoded keys).
+constexpr uint32_t kHasDescent = 1;      // some key[i] > key[i+1]
+constexpr uint32_t kHasNonDescent = 2;   // some key[i] <= key[i+1]
 
 constexpr int kMaxClasses = 8;          // finisher size classes
 
@@ -84,6 +94,7 @@ struct Ws {
     Bucket *list[2];               // two list slots: current level / next level
     uint32_t *hist[2];             // [bucket][kRadix]: counts, then exclusive prefix
     uint4 *andor[2];               // [bucket][2]: AND and OR of the encoded keys
+    uint32_t *order[2];            // [bucket]: kHasDescent | kHasNonDescent over adjacent keys
     uint32_t *tilemap;             // [tile] -> bucket index in the current list
     uint32_t *cells;               // [tile][kRadix] look-back cells
     Job *jobs;

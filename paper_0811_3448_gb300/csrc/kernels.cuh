@@ -475,6 +475,7 @@ static __global__ void k_prep(Ws ws, int slot) {
     for (long long b = gtid; b < nb; b += gstride) {
         ws.andor[slot][2 * b] = make_uint4(~0u, ~0u, ~0u, ~0u);
         ws.andor[slot][2 * b + 1] = make_uint4(0, 0, 0, 0);
+        ws.order[slot][b] = 0;
     }
     // tile map: CTA-per-bucket, threads stride over the bucket's tiles
     for (long long b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -507,6 +508,17 @@ __device__ __forceinline__ void unpack_chunk(const uint4 &v, typename KeyTraits<
     }
 }
 
+// The next lane's raw key (full warp).
+template <int KB>
+__device__ __forceinline__ typename KeyTraits<KB>::Raw shfl_down_raw(typename KeyTraits<KB>::Raw x) {
+    if constexpr (KB == 16) {
+        return make_uint4(__shfl_down_sync(0xffffffffu, x.x, 1), __shfl_down_sync(0xffffffffu, x.y, 1),
+                          __shfl_down_sync(0xffffffffu, x.z, 1), __shfl_down_sync(0xffffffffu, x.w, 1));
+    } else {
+        return __shfl_down_sync(0xffffffffu, x, 1);
+    }
+}
+
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
 template <int KB, bool IDENT>
 __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
@@ -523,17 +535,23 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     uint32_t *hist = slot ? ws.hist[1] : ws.hist[0];
     uint4 *andor = slot ? ws.andor[1] : ws.andor[0];
+    uint32_t *order = slot ? ws.order[1] : ws.order[0];
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     uint32_t *wh = sh[w];
     for (int i = tid; i < kWarps * kRadix; i += kThreads) (&sh[0][0])[i] = 0;
     Bits a = KT::ones(), o = KT::zero();
+    uint32_t ord = 0;   // order flags of the adjacent pairs this thread compared
     uint32_t cur_b = 0xffffffffu;   // bucket being accumulated (uniform across the CTA)
 
-    // flush the accumulated counts and AND / OR into bucket cur_b
+    // flush the accumulated counts, AND / OR and order flags into bucket cur_b
     auto flush = [&]() {
-        __syncthreads();
+        const int od = __syncthreads_or((int)(ord & kHasDescent));
+        const int on = __syncthreads_or((int)(ord & kHasNonDescent));
+        if (tid == 0 && (od || on))
+            atomicOr(&order[cur_b], (od ? kHasDescent : 0u) | (on ? kHasNonDescent : 0u));
+        ord = 0;
         uint32_t c = 0;
 #pragma unroll
         for (int ww = 0; ww < kWarps; ww++) {
@@ -601,18 +619,71 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
             const int shift = (int)((a1 - a0) / KB);
             const int nchunk = (int)((((a1 + (uintptr_t)tlen * KB + 15) & ~(uintptr_t)15) - a0) >> 4);
             const uint4 *c4 = reinterpret_cast<const uint4 *>(a0);
-#pragma unroll 4
-            for (int c = tid; c < nchunk; c += kThreads) {
-                Raw r[PER];
-                unpack_chunk<KB>(__ldg(c4 + c), r);
+            // every key of the tile is compared with its successor in the
+            // bucket (in the same chunk, in the next lane's chunk, or loaded
+            // when that chunk is not the next lane's), so each adjacent pair of the bucket
+            // is compared exactly once.  end_rel: the bucket's end, tile-relative.
+            const int end_rel = (int)((long long)bk.len - (tb - bk.begin));
+            constexpr int Q = 4;      // chunks in flight per thread
+            for (int cb = tid - lane; cb < nchunk; cb += Q * kThreads) {     // warp-uniform
+                Raw r[Q][PER];
 #pragma unroll
-                for (int e = 0; e < PER; e++) {
-                    const int idx = c * PER + e - shift;
-                    if (idx >= 0 && idx < tlen) {
-                        const Bits x = enc(r[e]);
-                        a = a & x;
-                        o = o | x;
-                        atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                for (int q = 0; q < Q; q++) {
+                    const int c = cb + q * kThreads + lane;
+                    if (c < nchunk) {
+                        unpack_chunk<KB>(__ldg(c4 + c), r[q]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < PER; e++) r[q][e] = Raw{};
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    const int c = cb + q * kThreads + lane;
+                    // once this thread has seen both a descent and a non-descent
+                    // the bucket's flags are settled and the comparisons stop
+                    const bool look = ord != (kHasDescent | kHasNonDescent);
+                    if (!__any_sync(0xffffffffu, look)) {
+                        // flags settled for the whole warp: counts only
+                        if (c >= nchunk) continue;
+#pragma unroll
+                        for (int e = 0; e < PER; e++) {
+                            const int idx = c * PER + e - shift;
+                            if (idx >= 0 && idx < tlen) {
+                                const Bits x = enc(r[q][e]);
+                                a = a & x;
+                                o = o | x;
+                                atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                            }
+                        }
+                        continue;
+                    }
+                    const bool has_after = look && (c + 1) * PER - shift < end_rel;
+                    Raw rafter = shfl_down_raw<KB>(r[q][0]);
+                    if (has_after && (lane == 31 || c + 1 >= nchunk)) {   // not in the next lane
+                        Raw rn[PER];
+                        unpack_chunk<KB>(__ldg(c4 + c + 1), rn);
+                        rafter = rn[0];
+                    }
+                    if (c >= nchunk) continue;
+#pragma unroll
+                    for (int e = 0; e < PER; e++) {
+                        const int idx = c * PER + e - shift;
+                        if (idx >= 0 && idx < tlen) {
+                            const Bits x = enc(r[q][e]);
+                            a = a & x;
+                            o = o | x;
+                            atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                            if (!look) {
+                            } else if (e + 1 < PER) {
+                                if (idx + 1 < end_rel) {
+                                    const Bits y = enc(r[q][e + 1 < PER ? e + 1 : e]);
+                                    ord |= KT::less(y, x) ? kHasDescent : kHasNonDescent;
+                                }
+                            } else if (has_after) {
+                                ord |= KT::less(enc(rafter), x) ? kHasDescent : kHasNonDescent;
+                            }
+                        }
                     }
                 }
             }
@@ -661,6 +732,36 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
         const int fd = KT::first_diff(a, o);
         const uint32_t cnt = ws.hist[slot][(size_t)b * kRadix + tid];
         const int nonzero = __syncthreads_count(cnt != 0);
+        // already in order ("Optimize the Algorithm": stop on a sorted
+        // sub-array): no adjacent descent -> finished as it stands; strictly
+        // decreasing -> finished by a reversal (no equal keys, so stable)
+        const uint32_t ord = ws.order[slot][b];
+        const bool counted = !(bk.flags & kHasHist) && bk.len > 1 && ord != 0;
+        const bool ascending = counted && !(ord & kHasDescent);
+        const bool descending = counted && !(ord & kHasNonDescent);
+        if (fd < W && (ascending || descending)) {
+            if (tid == 0) {
+                ws.list[slot][b].flags = bk.flags | kSkip;
+                if (descending || bk.buf == 1) {
+                    const uint32_t tiles = (uint32_t)(((long long)bk.len + T - 1) / T);
+                    const unsigned long long got = atomicAdd(
+                        &ws.ctr->copy_alloc, ((unsigned long long)tiles << 32) | 1ull);
+                    const uint32_t ci = (uint32_t)got;
+                    if (ci >= ws.ccap) {
+                        set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+                    } else {
+                        CopyJob cj;
+                        cj.begin = bk.begin | (descending ? kCopyReverse : 0LL) |
+                                   ((descending && bk.buf == 0) ? kCopyInPlace : 0LL);
+                        cj.len = bk.len;
+                        cj.tile_start = (uint32_t)(got >> 32);
+                        ws.copies[ci] = cj;
+                    }
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         if (fd >= W || nonzero <= 1) {
             // finished (all keys equal) or pass-through
             if (tid == 0) {
@@ -1588,13 +1689,38 @@ __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *key
             else hi = mid - 1;
         }
         const CopyJob cj = ws.copies[lo];
-        const long long a = cj.begin + (long long)(t - cj.tile_start) * T;
-        const long long e = min(a + T, cj.begin + (long long)cj.len);
-        const Raw *src = reinterpret_cast<const Raw *>(keys1);
-        Raw *dst = reinterpret_cast<Raw *>(keys0);
-        for (long long i = a + threadIdx.x; i < e; i += kThreads) {
-            dst[i] = src[i];
-            if (VB) reinterpret_cast<V *>(vals0)[i] = reinterpret_cast<const V *>(vals1)[i];
+        const long long cb = cj.begin & kCopyBeginMask;
+        const long long len = (long long)cj.len;
+        const long long j0 = (long long)(t - cj.tile_start) * T;      // job-relative
+        const long long j1 = min(j0 + T, len);
+        const bool rev = (cj.begin & kCopyReverse) != 0;
+        const bool inplace = (cj.begin & kCopyInPlace) != 0;
+        Raw *dst = reinterpret_cast<Raw *>(keys0) + cb;
+        V *vdst = VB ? reinterpret_cast<V *>(vals0) + cb : nullptr;
+        if (!rev || !inplace) {
+            // from the workspace arrays: straight, or reversed
+            const Raw *src = reinterpret_cast<const Raw *>(keys1) + cb;
+            const V *vsrc = VB ? reinterpret_cast<const V *>(vals1) + cb : nullptr;
+            for (long long i = j0 + threadIdx.x; i < j1; i += kThreads) {
+                const long long to = rev ? len - 1 - i : i;
+                dst[to] = src[i];
+                if (VB) vdst[to] = vsrc[i];
+            }
+        } else {
+            // reversed in place: the thread of position i < len-1-i swaps the pair
+            for (long long i = j0 + threadIdx.x; i < j1; i += kThreads) {
+                const long long k = len - 1 - i;
+                if (i < k) {
+                    const Raw x = dst[i];
+                    dst[i] = dst[k];
+                    dst[k] = x;
+                    if (VB) {
+                        const V y = vdst[i];
+                        vdst[i] = vdst[k];
+                        vdst[k] = y;
+                    }
+                }
+            }
         }
     }
 }

@@ -55,7 +55,7 @@ inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 20
 inline int levels_for(int kb) { return 8 * kb / kBits; }
 
 struct Layout {
-    size_t ctr, altk, altv, list[2], hist[2], andor[2], tilemap, cells, jobs, jobidx, jobs2, copies, total;
+    size_t ctr, altk, altv, list[2], hist[2], andor[2], order[2], tilemap, cells, jobs, jobidx, jobs2, copies, total;
     uint32_t mcap, tcap, jcap, ccap;
 };
 
@@ -89,6 +89,7 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
         L.list[s] = take((size_t)m * sizeof(Bucket));
         L.hist[s] = take((size_t)m * kRadix * sizeof(uint32_t));
         L.andor[s] = take((size_t)m * 2 * sizeof(uint4));
+        L.order[s] = take((size_t)m * sizeof(uint32_t));
     }
     L.tilemap = take((size_t)t * sizeof(uint32_t));
     L.cells = take((size_t)t * kRadix * sizeof(uint32_t));
@@ -110,6 +111,7 @@ inline Ws carve(const Layout &L, void *base) {
         ws.list[s] = reinterpret_cast<Bucket *>(b + L.list[s]);
         ws.hist[s] = reinterpret_cast<uint32_t *>(b + L.hist[s]);
         ws.andor[s] = reinterpret_cast<uint4 *>(b + L.andor[s]);
+        ws.order[s] = reinterpret_cast<uint32_t *>(b + L.order[s]);
     }
     ws.tilemap = reinterpret_cast<uint32_t *>(b + L.tilemap);
     ws.cells = reinterpret_cast<uint32_t *>(b + L.cells);

@@ -76,6 +76,7 @@ Layout pass_layout(long long n, int kb) {
         L.list[s] = take((size_t)m * sizeof(Bucket));
         L.hist[s] = take((size_t)m * kRadix * sizeof(uint32_t));
         L.andor[s] = take((size_t)m * 2 * sizeof(uint4));
+        L.order[s] = take((size_t)m * sizeof(uint32_t));
     }
     L.tilemap = take((size_t)t * sizeof(uint32_t));
     L.cells = take((size_t)t * kRadix * sizeof(uint32_t));
