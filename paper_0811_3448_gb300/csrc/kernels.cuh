@@ -1666,6 +1666,25 @@ __global__ void __launch_bounds__(kThreads, 2)
 // arrays go back to the caller's arrays.  Tiles by ticket; the job of a tile is
 // found by binary search on tile_start (increasing with the job index).
 // ---------------------------------------------------------------------------
+// Copies count elements by the whole CTA: 16-byte vectors when source and
+// destination share their alignment modulo 16 (after a scalar head up to the
+// boundary), scalar otherwise and for the tail.
+template <typename E>
+__device__ __forceinline__ void copy_range(E *dst, const E *src, long long count) {
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst), s = reinterpret_cast<uintptr_t>(src);
+    long long head = count;
+    if (((d ^ s) & 15) == 0) head = min(count, (long long)(((16 - (d & 15)) & 15) / sizeof(E)));
+    for (long long i = threadIdx.x; i < head; i += kThreads) dst[i] = src[i];
+    const long long nvec = (count - head) * (long long)sizeof(E) / 16;
+    uint4 *dv = reinterpret_cast<uint4 *>(dst + head);
+    const uint4 *sv = reinterpret_cast<const uint4 *>(src + head);
+#pragma unroll 4
+    for (long long v = threadIdx.x; v < nvec; v += kThreads) dv[v] = __ldg(sv + v);
+    for (long long i = head + nvec * (16 / (long long)sizeof(E)) + threadIdx.x; i < count;
+         i += kThreads)
+        dst[i] = src[i];
+}
+
 template <int KB, int VB>
 __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *keys1, void *vals0,
                                                    void *vals1) {
@@ -1697,14 +1716,17 @@ __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *key
         const bool inplace = (cj.begin & kCopyInPlace) != 0;
         Raw *dst = reinterpret_cast<Raw *>(keys0) + cb;
         V *vdst = VB ? reinterpret_cast<V *>(vals0) + cb : nullptr;
-        if (!rev || !inplace) {
-            // from the workspace arrays: straight, or reversed
+        if (!rev) {
+            // from the workspace arrays, straight
+            copy_range<Raw>(dst + j0, reinterpret_cast<const Raw *>(keys1) + cb + j0, j1 - j0);
+            if (VB) copy_range<V>(vdst + j0, reinterpret_cast<const V *>(vals1) + cb + j0, j1 - j0);
+        } else if (!inplace) {
+            // from the workspace arrays, reversed
             const Raw *src = reinterpret_cast<const Raw *>(keys1) + cb;
             const V *vsrc = VB ? reinterpret_cast<const V *>(vals1) + cb : nullptr;
             for (long long i = j0 + threadIdx.x; i < j1; i += kThreads) {
-                const long long to = rev ? len - 1 - i : i;
-                dst[to] = src[i];
-                if (VB) vdst[to] = vsrc[i];
+                dst[len - 1 - i] = src[i];
+                if (VB) vdst[len - 1 - i] = vsrc[i];
             }
         } else {
             // reversed in place: the thread of position i < len-1-i swaps the pair
