@@ -107,8 +107,8 @@ int check_types(int key_bytes, int map, int val_bytes) {
 }
 
 // Resolves a (nullable) config for the key size into the call.
-int resolve_config(const binar_config *cfg, int key_bytes, Call &c) {
-    const int T = tile_for(key_bytes);
+int resolve_config(const binar_config *cfg, int key_bytes, int val_bytes, Call &c) {
+    const int T = tile_for(key_bytes, val_bytes);
     const int cap = finish_cap_for(key_bytes);
     c.cutoff = cap;
     c.ctas_per_sm = 0;
@@ -172,7 +172,7 @@ static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int
     if (ws_bytes < make_layout(n, segs, key_bytes, val_bytes).total)
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
-    if ((rc = resolve_config(cfg, key_bytes, c))) return rc;
+    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c))) return rc;
     if (n == 0 || (d_offsets && num_segments == 0)) {
         // nothing to sort; the status word still reports this call
         if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream)) !=
@@ -235,7 +235,7 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
     if (ws_bytes < make_layout(n, 1, key_bytes, val_bytes).total)
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
-    if ((rc = resolve_config(cfg, key_bytes, c))) return rc;
+    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) {
         if (d_offsets &&

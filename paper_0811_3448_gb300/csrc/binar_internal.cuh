@@ -113,6 +113,7 @@ struct Params {
     int cutoff;                    // finisher cutoff C
     long long timeout_ns;
     int skip_publish_tile;         // test hook: level-0 tile that never publishes (-1 = none)
+    int tile;                      // keys per partition tile for this key / payload width
 };
 
 // ---------------------------------------------------------------------------

@@ -50,7 +50,7 @@ int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0
 
 template <int KB, int VB>
 int run_call_vb(const Call &c) {
-    constexpr int T = PartShape<KB>::kTile;
+    constexpr int T = PartShape<KB, VB>::kTile;
     constexpr int STABLE = VB > 0;
     const int L = levels_for(KB);
     const int sms = device_sms();
@@ -63,6 +63,7 @@ int run_call_vb(const Call &c) {
     p.cutoff = c.cutoff;
     p.timeout_ns = c.timeout_ns;
     p.skip_publish_tile = c.skip_publish_tile;
+    p.tile = T;
     const int small_grid = sms * 4;
     int rc;
 

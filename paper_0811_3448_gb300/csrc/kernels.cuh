@@ -25,12 +25,15 @@ template <int KB> struct TileShape {
     static constexpr int kItems = KB == 4 ? 32 : (KB == 8 ? 16 : 8);
     static constexpr int kTile = kThreads * kItems;
 };
-// Items per thread of a partition / histogram tile: 4096 / 2048 / 2048 keys;
-// resident partition CTAs per SM the register budget is sized for.
-template <int KB> struct PartShape {
-    static constexpr int kItems = KB == 4 ? 16 : 8;
+// Items per thread of a partition / histogram tile -- 6144 keys for 4-byte keys
+// without payload, 4096 for 4-byte keys with one, 2048 for wider keys -- and
+// the resident partition CTAs per SM the register budget is sized for.  Every
+// kernel of a call uses the same tile (Params::tile).
+template <int KB, int VB> struct PartShape {
+    static constexpr bool kWide = KB == 4 && VB == 0;
+    static constexpr int kItems = kWide ? 24 : (KB == 4 ? 16 : 8);
     static constexpr int kTile = kThreads * kItems;
-    static constexpr int kMinBlocks = KB == 16 ? 3 : 4;
+    static constexpr int kMinBlocks = kWide ? 3 : (KB == 16 ? 3 : 4);
 };
 
 // ---------------------------------------------------------------------------
@@ -525,7 +528,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
-    constexpr int T = PartShape<KB>::kTile;
+    const int T = p.tile;
     constexpr int PER = 16 / KB;
     __shared__ uint32_t sh[kWarps][kRadix];
     __shared__ uint4 sand[kWarps], sor[kWarps];
@@ -709,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     using KT = KeyTraits<KB>;
     using Bits = typename KT::Bits;
     constexpr int W = KT::kW;
-    constexpr int T = PartShape<KB>::kTile;
+    const int T = p.tile;
     __shared__ uint32_t scount[kRadix];
     __shared__ uint32_t sexcl[kRadix];
     __shared__ uint32_t scratch[kWarps];
@@ -987,7 +990,7 @@ constexpr int kLookbackWindow = 8;
 
 template <int KB, int VB, bool STABLE>
 struct PartitionSmem {
-    static constexpr int T = PartShape<KB>::kTile;
+    static constexpr int T = PartShape<KB, VB>::kTile;
     typename RankSmemFor<STABLE>::T rank;
     int offs[kRadix];          // bucket-relative destination of digit d's run, minus its tile start
     uint32_t next_ticket;
@@ -1049,19 +1052,23 @@ __device__ __forceinline__ uint32_t lookback(const Ws &ws, const Params &p, uint
 
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
 template <int KB, int VB, bool STABLE, bool IDENT>
-__global__ void __launch_bounds__(kThreads, PartShape<KB>::kMinBlocks)
+__global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
     k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
                 void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int ITEMS = PartShape<KB>::kItems;
-    constexpr int T = PartShape<KB>::kTile;
+    constexpr int ITEMS = PartShape<KB, VB>::kItems;
+    constexpr int T = PartShape<KB, VB>::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
+    if (p.tile != T) {            // the call's tiles must be this kernel's
+        if (threadIdx.x == 0) set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+        return;
+    }
     const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     const uint32_t *prefix = slot ? ws.hist[1] : ws.hist[0];
@@ -1690,7 +1697,7 @@ __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *key
                                                    void *vals1) {
     using Raw = typename KeyTraits<KB>::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int T = PartShape<KB>::kTile;
+    constexpr int T = PartShape<KB, VB>::kTile;
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
     const unsigned long long ca = ws.ctr->copy_alloc;

@@ -50,7 +50,8 @@ int launch(const char *name, int index, cudaStream_t s, F &&f) {
 constexpr int kMinCutoff = 2048;
 
 // keys per partition tile, and the finisher's largest job (= the largest cutoff)
-inline int tile_for(int kb) { return kb == 4 ? 4096 : 2048; }
+// keys per partition tile (kernels.cuh PartShape)
+inline int tile_for(int kb, int vb) { return kb == 4 ? (vb == 0 ? 6144 : 4096) : 2048; }
 inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
 inline int levels_for(int kb) { return 8 * kb / kBits; }
 
@@ -63,7 +64,7 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     Layout L{};
-    const long long T = tile_for(kb), lv = levels_for(kb);
+    const long long T = tile_for(kb, vb), lv = levels_for(kb);
     const long long m = n / (kMinCutoff + 1) + segs + 2;
     const long long t = n / T + m + 2;
     // jobs of a level: own jobs (>= C/8 keys) and merged runs (two adjacent

@@ -54,9 +54,9 @@ int scratch_address(void **out) {
 
 // The pass needs the counters, one bucket slot, histograms, the tile map and
 // the look-back cells -- not the ping-pong buffers or the finisher lists.
-Layout pass_layout(long long n, int kb) {
+Layout pass_layout(long long n, int kb, int vb) {
     Layout L{};
-    const long long T = tile_for(kb);
+    const long long T = tile_for(kb, vb);
     const long long m = 3;
     const long long t = n / T + 2;
     L.mcap = (uint32_t)m;
@@ -111,7 +111,7 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
         (!d_vals_in || !d_vals_out || !aligned_to(d_vals_in, val_bytes) ||
          !aligned_to(d_vals_out, val_bytes)))
         return BINAR_ERR_INVALID_ARG;
-    const Layout lay = pass_layout(n, key_bytes);
+    const Layout lay = pass_layout(n, key_bytes, val_bytes);
     if (lay.total > kScratchBytes) return BINAR_ERR_WORKSPACE_TOO_SMALL;   // n above the limit
     void *scratch = nullptr;
     int rc = scratch_address(&scratch);
