@@ -73,8 +73,8 @@ typedef enum {
  * defaults. */
 typedef struct {
     int tile_keys;          /* keys per partition tile: 0 or the width's tile --
-                               6144 (4-byte keys, no payload), 4096 (4-byte keys
-                               with payload), 2048 (8- and 16-byte keys) */
+                               6144 (4-byte keys), 3072 (8-byte keys), 2048
+                               (16-byte keys) */
     int bits_per_pass;      /* k, key bits consumed per partition pass: 0 or 8 */
     int small_cutoff;       /* C: buckets of <= C keys are finished in shared memory;
                                2048 .. the finisher capacity for the key/payload size */
