@@ -63,6 +63,8 @@ def parse_args():
                          "20,000 log-uniform ones")
     ap.add_argument("--no-plain", action="store_true",
                     help="segments: skip the one-call-per-segment comparison")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="segments: library defaults instead of the autotuned configuration")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="serve: device-memory budget")
@@ -535,7 +537,10 @@ def run_segments(args):
     v0 = torch.from_numpy(vals_h).to(dev)
     k, v = k0.clone(), v0.clone()
     segs = len(off_h) - 1
-    cfg, timings = autotune.tune(k0, v0, off)
+    if args.no_autotune:
+        cfg, timings = binding.Config(), {}
+    else:
+        cfg, timings = autotune.tune(k0, v0, off)
     ws = binding.workspace(n, 4, 4, segs, device=dev)
     binding.sort_segmented(k, off, v, ws=ws, config=cfg)      # set-up before capture
     torch.cuda.synchronize()
