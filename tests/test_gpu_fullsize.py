@@ -74,3 +74,77 @@ def test_full_size_keys_only_uniform_u32():
     # same multiset: both sorted copies agree with a library sort of the input
     ref = torch.sort(k0.to(torch.int64)).values
     assert bool((ref == k).all())
+
+
+def _check_stable_by_order_key(torch, okey_in, okey_out, vals_out, eq_out=None):
+    """okey_*: int64 tensors (or tuples of them, compared lexicographically) whose
+    order is the key order; checks the stable-sort properties of the output."""
+    if not isinstance(okey_out, tuple):
+        okey_in, okey_out = (okey_in,), (okey_out,)
+    v = vals_out.to(torch.int64)
+    n = v.shape[0]
+    assert bool((torch.bincount(v, minlength=n) == 1).all()), "payload not a permutation"
+    for a, b in zip(okey_in, okey_out):
+        assert bool((a[v] == b).all()), "key / payload mismatch"
+    # nondecreasing, lexicographically
+    less = torch.zeros(n - 1, dtype=torch.bool, device=v.device)
+    equal = torch.ones(n - 1, dtype=torch.bool, device=v.device)
+    for b in okey_out:
+        less |= equal & (b[:-1] < b[1:])
+        equal &= b[:-1] == b[1:]
+    assert bool((less | equal).all()), "keys not sorted"
+    assert bool((v[1:][equal] > v[:-1][equal]).all()), "equal keys out of input order"
+
+
+def test_full_size_config3_float32_pairs():
+    """64M float32 (normal mixed with +-0, +-inf, denormals, duplicates)."""
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    n = 64 << 20
+    keys = inputs.config3_f32(n)
+    k0 = torch.from_numpy(keys).cuda()
+    tk, tv = k0.clone(), torch.from_numpy(inputs.index_payload(n)).cuda()
+    ws = binding.workspace(n, 4, 4)
+    binding.sort_pairs(tk, tv, ws=ws)
+    binding.check_status(ws)
+
+    def order(t):   # IEEE order of the bit patterns (-0 < +0, NaNs by sign)
+        u = t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        return torch.where(u >= 2 ** 31, (~u) & 0xFFFFFFFF, u | 2 ** 31)
+    _check_stable_by_order_key(torch, order(k0), order(tk), tv)
+
+
+def test_full_size_config3_int64_pairs():
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    n = 64 << 20
+    k0 = torch.from_numpy(inputs.config3_i64(n)).cuda()
+    tk, tv = k0.clone(), torch.from_numpy(inputs.index_payload(n)).cuda()
+    ws = binding.workspace(n, 8, 4)
+    binding.sort_pairs(tk, tv, ws=ws)
+    binding.check_status(ws)
+    _check_stable_by_order_key(torch, k0, tk, tv)
+
+
+@pytest.mark.parametrize("shared_prefix", [False, True])
+def test_full_size_config3_bytes16_pairs(shared_prefix):
+    """16M 16-byte strings in memcmp order (uniform bytes, or a shared 12-byte prefix)."""
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    n = 16 << 20
+    k0 = torch.from_numpy(inputs.config3_bytes16(n, shared_prefix=shared_prefix)).cuda()
+    tk, tv = k0.clone(), torch.from_numpy(inputs.index_payload(n)).cuda()
+    ws = binding.workspace(n, 16, 4)
+    binding.sort_pairs(tk, tv, ws=ws)
+    binding.check_status(ws)
+
+    def order(t):   # big-endian halves, as signed int64 with the sign bit flipped
+        b = t.to(torch.int64)
+        hi = torch.zeros(t.shape[0], dtype=torch.int64, device=t.device)
+        lo = torch.zeros_like(hi)
+        for i in range(8):
+            hi = (hi << 8) | b[:, i]
+            lo = (lo << 8) | b[:, 8 + i]
+        flip = torch.tensor(-(2 ** 63), dtype=torch.int64, device=t.device)
+        return hi ^ flip, lo ^ flip
+    _check_stable_by_order_key(torch, order(k0), order(tk), tv)
