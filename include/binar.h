@@ -150,7 +150,8 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
  * memory through a fixed pool with a hard budget, or a latency-critical loop
  * that must not call (and synchronise on) cudaMalloc.
  *   Arguments, layout and results as binar_partition_pass.
- *   Limit: n <= about 16M keys of 4 bytes, about 8M keys of 8 or 16 bytes;
+ *   Limit: n <= 25,006,079 keys of 4 bytes, 12,503,039 of 8 bytes,
+ *   8,335,359 of 16 bytes (the look-back state of one pass in 4 MiB);
  *   larger n returns BINAR_ERR_WORKSPACE_TOO_SMALL before any work.
  *   The first call on a device looks up the scratch array's device address
  *   (host-side set-up); make that first call before any stream capture.
