@@ -71,6 +71,8 @@ def parse_args():
     ap.add_argument("--span-log2", type=int, default=16,
                     help="serve: request sizes floor(2^(10 + span U)) keys (16: 1K..64M)")
     ap.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
+    ap.add_argument("--plain-slots", type=int, default=0,
+                    help="serve: stream slots of the one-request-per-launch form (0: --slots)")
     args = ap.parse_args()
     if args.n <= 0:
         args.n = (128 << 20) if (args.key == "u64" and args.workload == "pairs") else (256 << 20)

@@ -433,9 +433,11 @@ def bench_main(args) -> Optional[dict]:
     warm_up()
     torch.cuda.synchronize()
     out = {}
+    plain_slots = getattr(args, "plain_slots", 0) or slots
     for mode in ("batched", "plain"):
         reqs = requests_from_mix(mix)
-        srv = Server(budget_bytes=budget, slots=slots, mode=mode)
+        srv = Server(budget_bytes=budget, slots=slots if mode == "batched" else plain_slots,
+                     mode=mode)
         sample = {r.rid for r in reqs[::max(1, len(reqs) // 16)] if r.n <= (4 << 20)}
         out[mode] = srv.run(reqs, keep=lambda r: r.rid in sample)
         # sampled check: each kept result equals the same request sorted alone
@@ -448,6 +450,7 @@ def bench_main(args) -> Optional[dict]:
             if not torch.equal(k.view(torch.uint8), ak.view(torch.uint8)) or \
                     (v is not None and not torch.equal(v, av)):
                 mism += 1
+        out[mode]["slots"] = len(srv.streams)
         out[mode]["sampled_checks"] = len(srv.kept)
         out[mode]["sampled_mismatches"] = mism
         del srv
