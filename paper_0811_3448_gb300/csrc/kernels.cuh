@@ -26,13 +26,13 @@ template <int KB> struct TileShape {
     static constexpr int kTile = kThreads * kItems;
 };
 // Items per thread of a partition / histogram tile -- 6144 keys for 4-byte
-// keys, 3072 for 8-byte keys, 2048 for 16-byte keys -- and the resident
+// keys, 4096 for 8-byte keys, 2048 for 16-byte keys -- and the resident
 // partition CTAs per SM the register budget is sized for (3: measured against
 // 4096 / 2048-key tiles at 4 CTAs/SM, the larger tiles spread the per-tile
 // ticket, scan and look-back over more keys).  Every kernel of a call uses the
 // same tile (Params::tile).
 template <int KB, int VB> struct PartShape {
-    static constexpr int kItems = KB == 4 ? 24 : (KB == 8 ? 12 : 8);
+    static constexpr int kItems = KB == 4 ? 24 : (KB == 8 ? 16 : 8);
     static constexpr int kTile = kThreads * kItems;
     static constexpr int kMinBlocks = 3;
 };
