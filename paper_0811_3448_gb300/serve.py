@@ -265,6 +265,7 @@ class Server:
         self.kept = {}
         self.batches = 0
         self.batch_sizes = []
+        self.failed_launches = 0
 
     # -- device views of a block
     def _views(self, b: Batch):
@@ -282,8 +283,27 @@ class Server:
         return keys, vals, offs, ws
 
     def _launch(self, b: Batch, now: float) -> None:
-        torch, binding = self.torch, self.binding
         b.slot = self.free_slots.pop()
+        try:
+            self._enqueue(b)
+        except Exception as e:    # the batch fails; its slot and memory come back
+            for r in b.requests:
+                r.status = "failed"
+                r.error = f"launch: {e}"
+                r.t_launch = r.t_done = now
+            self.sched.release(b)
+            self.free_slots.append(b.slot)
+            self.failed_launches += 1
+            return
+        for r in b.requests:
+            r.status = "running"
+            r.t_launch = now
+        self.inflight.append(b)
+        self.batches += 1
+        self.batch_sizes.append(len(b.requests))
+
+    def _enqueue(self, b: Batch) -> None:
+        torch, binding = self.torch, self.binding
         s = self.streams[b.slot]
         keys, vals, offs, ws = self._views(b)
         with torch.cuda.stream(s):
@@ -302,12 +322,6 @@ class Server:
                 binding.sort_keys(keys, ws=ws, config=self.config, stream=s)
             b.event = torch.cuda.Event()
             b.event.record(s)
-        for r in b.requests:
-            r.status = "running"
-            r.t_launch = now
-        self.inflight.append(b)
-        self.batches += 1
-        self.batch_sizes.append(len(b.requests))
 
     def _complete(self, b: Batch, now: float, keep) -> None:
         binding = self.binding
@@ -376,7 +390,7 @@ class Server:
                 "mean_ms": float(np.mean(lat)) if lat else None,
                 "max_ms": max(lat) if lat else None,
                 "queue_wait_p50_ms": percentile(wait, 50), "queue_wait_p99_ms": percentile(wait, 99),
-                "launches": self.batches,
+                "launches": self.batches, "failed_launches": self.failed_launches,
                 "mean_requests_per_launch": float(np.mean(self.batch_sizes)) if self.batch_sizes
                 else None,
                 "peak_budget_bytes": self.arena.peak, "budget_bytes": self.arena.capacity}

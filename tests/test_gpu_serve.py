@@ -106,3 +106,32 @@ def test_budget_rejects_oversize_and_serves_the_rest():
         assert same_bits(to_host(k), ek)
         if r.has_payload:
             assert same_bits(to_host(v).view(np.uint32), ev)
+
+
+def test_failed_launch_releases_its_slot_and_memory(monkeypatch):
+    """A batch whose launch raises is marked failed; its stream slot and arena
+    block come back and the other requests are still served."""
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    reqs = [serve.Request(rid=i, n=5000 + i, key_type="u32", has_payload=False, seed=i,
+                          arrival_s=0.001 * i) for i in range(6)]
+    srv = serve.Server(budget_bytes=64 << 20, slots=1, mode="plain")
+    real = binding.sort_keys
+    calls = {"n": 0}
+
+    def flaky(*a, **k):
+        calls["n"] += 1
+        if calls["n"] == 3:
+            raise binding.BinarError(binding.ERR_INVALID_ARG, "test")
+        return real(*a, **k)
+    monkeypatch.setattr(binding, "sort_keys", flaky)
+    st = srv.run(reqs, keep=lambda r: True, max_wall_s=60)
+    assert st["failed"] == 1 and st["done"] == 5 and st["failed_launches"] == 1
+    assert srv.arena.used == 0 and srv.free_slots == [0]
+    failed = [r for r in reqs if r.status == "failed"]
+    assert len(failed) == 1 and failed[0].error.startswith("launch:")
+    for r in reqs:
+        if r.status == "done":
+            k, _ = srv.kept[r.rid]
+            ak, _ = serve.sort_alone(r)
+            assert torch.equal(k, ak)
