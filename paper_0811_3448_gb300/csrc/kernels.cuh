@@ -978,8 +978,8 @@ static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long lon
 
 // ---------------------------------------------------------------------------
 // partition: one tile per ticket.  The tile's keys and payloads are copied
-// into shared memory with 16-byte cp.async (from the 16-byte boundary at or
-// below the tile's first element), the keys move to registers and are ranked
+// into shared memory by the bulk-copy engine (the 16-byte chunks from the
+// boundary at or below the tile's first element, completing on an mbarrier), the keys move to registers and are ranked
 // by digit (digits and ranks packed in registers), and the tile is staged in
 // shared memory in sorted order, in place: keys first, then payloads.  The
 // tile is placed after its predecessors in the same bucket through a
@@ -1000,23 +1000,57 @@ struct PartitionSmem {
     typename RankSmemFor<STABLE>::T rank;
     int offs[kRadix];          // bucket-relative destination of digit d's run, minus its tile start
     uint32_t next_ticket;
+    alignas(8) unsigned long long bar;     // mbarrier of the tile's bulk copies
     alignas(16) unsigned char keys[T * KB + 16];
     alignas(16) unsigned char vals[VB ? T * VB + 16 : 16];
 };
 
-// Issues cp.async copies of the 16-byte chunks that hold elements [0, len) of
-// src (EB-byte elements, src aligned to EB) into dst, starting from the chunk
-// boundary at or below src; returns the index of src[0] in dst.  Every chunk
-// read holds at least one element of the range.  dst holds len * EB + 16 bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// The 16-byte aligned chunk range [*a0, *a0 + *bytes) that holds elements
+// [0, len) of src (EB-byte elements, src aligned to EB); returns the index of
+// src[0] in it.
 template <int EB>
-__device__ __forceinline__ int stage_in(unsigned char *dst, const void *src, int len) {
+__device__ __forceinline__ int chunk_range(const void *src, int len, uintptr_t *a0, uint32_t *bytes) {
     const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-    const uintptr_t a0 = a & ~(uintptr_t)15;
+    *a0 = a & ~(uintptr_t)15;
     const uintptr_t a1 = (a + (uintptr_t)len * EB + 15) & ~(uintptr_t)15;
-    const int nchunk = (int)((a1 - a0) >> 4);
-    for (int c = threadIdx.x; c < nchunk; c += kThreads)
-        cp_async<16>(dst + 16 * c, reinterpret_cast<const void *>(a0 + 16 * (uintptr_t)c));
-    return (int)((a - a0) / EB);
+    *bytes = (uint32_t)(a1 - *a0);
+    return (int)((a - *a0) / EB);
+}
+
+// Tile loads by the bulk-copy (TMA) engine: one thread starts the copies of a
+// tile, which complete on a shared-memory mbarrier; every thread then waits on
+// the barrier's phase.  bulk_begin: the previous use of the destination
+// (ordered by a __syncthreads before the call) comes before the async writes.
+__device__ __forceinline__ void mbar_init(void *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_begin(void *bar, uint32_t bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, uintptr_t src, uint32_t bytes, void *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+// Waits for phase `parity` of the barrier; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(void *bar, uint32_t parity, long long limit_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if ((long long)(globaltimer_ns() - t0) > limit_ns) return false;
+    }
 }
 
 // Sum of the counts of digit threadIdx.x over tiles first .. t-1 back to the
@@ -1084,6 +1118,9 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
     if constexpr (STABLE) {
         for (int i = tid & 31; i < kRadix; i += 32) s.rank.wmask[(tid >> 5) * kRadix + i] = 0;
     }
+    if (tid == 0) mbar_init(&s.bar);
+    __syncthreads();
+    uint32_t phase = 0;
     for (;;) {
         if (tid == 0) s.next_ticket = atomicAdd(&ws.ctr->ticket_part, 1u);
         __syncthreads();
@@ -1101,10 +1138,23 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
         Raw *dst = reinterpret_cast<Raw *>(bk.buf ? keys0 : keys1) + bk.begin;
         V *vdst = VB ? reinterpret_cast<V *>(bk.buf ? vals0 : vals1) + bk.begin : nullptr;
 
-        const int ks = stage_in<KB>(s.keys, src, tlen);
-        const int vs = VB ? stage_in<VB>(s.vals, vsrc, tlen) : 0;
-        cp_async_wait_all();
-        __syncthreads();
+        // the tile's 16-byte chunks, by the bulk-copy engine
+        uintptr_t ka0 = 0, va0 = 0;
+        uint32_t kbytes = 0, vbytes = 0;
+        const int ks = chunk_range<KB>(src, tlen, &ka0, &kbytes);
+        const int vs = VB ? chunk_range<VB>(vsrc, tlen, &va0, &vbytes) : 0;
+        if (tid == 0) {
+            bulk_begin(&s.bar, kbytes + vbytes);
+            bulk_load(s.keys, ka0, kbytes, &s.bar);
+            if (VB) bulk_load(s.vals, va0, vbytes, &s.bar);
+        }
+        const bool landed = mbar_wait(&s.bar, phase, p.timeout_ns);
+        if (__syncthreads_or(!landed)) {                  // uniform across the CTA
+            if (tid == 0) set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
+            if (!landed) mbar_wait(&s.bar, phase, p.timeout_ns);   // the copy in flight, bounded
+            return;
+        }
+        phase ^= 1;
 
         Raw k[ITEMS];
         Packed<ITEMS> pk;
@@ -1209,6 +1259,7 @@ struct FinishSmem {
     uint4 sand[kWarps], sor[kWarps];
     uint32_t next_ticket;
     Job next_job;
+    alignas(8) unsigned long long bar;     // mbarrier of the job's bulk copies
     alignas(16) unsigned char keys[T * KB + 16];
     alignas(16) unsigned char vals[VB ? T * VB + 16 : 16];
     uint16_t perm[T];
@@ -1490,7 +1541,9 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
     if (count == 0 || base + count > ws.jcap) return;
     const uint32_t *mine = ws.jobidx + base;
     const int tid = threadIdx.x;
+    uint32_t phase = 0;
     if (tid == 0) {
+        mbar_init(&s.bar);
         const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
         s.next_ticket = t;
         if (t < count) s.next_job = ws.jobs[mine[t]];
@@ -1508,9 +1561,16 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
         V *vdst = VB ? reinterpret_cast<V *>(vals0) + job.begin : nullptr;
         const bool trivial = job.pos >= W || len <= 1 || len > kThreads * IU;
         int ks = 0, vs = 0;
-        if (!trivial) {
-            ks = stage_in<KB>(s.keys, src, len);
-            if (VB) vs = stage_in<VB>(s.vals, vsrc, len);
+        if (!trivial) {   // the job's 16-byte chunks, by the bulk-copy engine
+            uintptr_t ka0 = 0, va0 = 0;
+            uint32_t kbytes = 0, vbytes = 0;
+            ks = chunk_range<KB>(src, len, &ka0, &kbytes);
+            if (VB) vs = chunk_range<VB>(vsrc, len, &va0, &vbytes);
+            if (tid == 0) {
+                bulk_begin(&s.bar, kbytes + vbytes);
+                bulk_load(s.keys, ka0, kbytes, &s.bar);
+                if (VB) bulk_load(s.vals, va0, vbytes, &s.bar);
+            }
         }
         if (tid == 0) {   // the next job, while this one's data arrives
             const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
@@ -1528,8 +1588,13 @@ __global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3
             }
             continue;
         }
-        cp_async_wait_all();
-        __syncthreads();
+        const bool landed = mbar_wait(&s.bar, phase, p.timeout_ns);
+        if (__syncthreads_or(!landed)) {                  // uniform across the CTA
+            if (tid == 0) set_status(ws.ctr, BINAR_ERR_DEVICE_TIMEOUT);
+            if (!landed) mbar_wait(&s.bar, phase, p.timeout_ns);   // the copy in flight, bounded
+            return;
+        }
+        phase ^= 1;
         if (!finish_fast<KB, VB, IU>(s, ws, enc, dec, job, ks, vs, dst, vdst) && tid == 0) {
             // runs too long for the fast path: the job goes to the LSD path
             const uint32_t ji = atomicAdd(&ws.ctr->njobs2, 1u);
