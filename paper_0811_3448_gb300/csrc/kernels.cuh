@@ -1522,8 +1522,14 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
 }
 
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
+// Resident CTAs per SM the finisher's registers are sized for: 4 for keys
+// without payload in classes of up to 16 items per thread (their shared memory
+// leaves room; measured faster despite a few spilled registers), 3 up to 18
+// items, 2 above.
 template <int KB, int VB, int CLS, bool IDENT>
-__global__ void __launch_bounds__(kThreads, FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CLS) <= 16)
+                                                ? 4
+                                                : (FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2))
     k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
