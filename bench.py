@@ -104,9 +104,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernels have not changed since it was taken; else None."""
+def recorded_traffic(kernel: str, key_bytes: int, val_bytes: int, n: int):
+    """DRAM bytes per launch of `kernel` on n records of this key / payload
+    width, from the committed ncu summary: its per-record traffic (taken on a
+    smaller case of the same widths) times n.  None if the kernels have changed
+    since it was taken or it holds no capture of these widths."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -115,7 +117,10 @@ def recorded_traffic(kernel: str):
     if d.get("source_hash") != kernel_source_hash():
         return None
     ent = d.get("kernels", {}).get(kernel)
-    return None if ent is None else ent.get("dram_bytes_per_launch_full_size")
+    if ent is None or ent.get("key_bytes") != key_bytes or ent.get("val_bytes") != val_bytes:
+        return None
+    per_key = (ent["dram_bytes_read"] + ent["dram_bytes_write"]) / ent["measured_keys"]
+    return int(round(per_key * n))
 
 
 class ClockSampler:
@@ -460,7 +465,7 @@ def run_binar(args):
         roofline = {"bound": "hbm", "kernel": "partition[0]", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst)",
-                    "traffic": recorded_traffic("partition[0]"),
+                    "traffic": recorded_traffic("partition[0]", kb, 4, n),
                     "algorithmic_bytes_per_launch": alg_bytes,
                     "frac_of_8TBs_spec": achieved / 8000.0}
     dominant = max(kernels.items(), key=lambda kv: kv[1]["share"])[0] if kernels else None

@@ -1,5 +1,7 @@
 """Full-size sorts in the configuration bench.py times (256M uint32 keys and
-128M uint64 keys with uint32 payloads equal to the original index).
+128M uint64 keys with uint32 payloads equal to the original index), the other
+configurations at their full sizes, and the largest sizes: 1G records and the
+largest array the C ABI accepts (2^31 - 2 records, 8 GiB per array).
 
 At these sizes the oracle cannot recompute the output, so the checks are
 properties that together fix the unique stable sort, whatever the size:
@@ -148,3 +150,48 @@ def test_full_size_config3_bytes16_pairs(shared_prefix):
         flip = torch.tensor(-(2 ** 63), dtype=torch.int64, device=t.device)
         return hi ^ flip, lo ^ flip
     _check_stable_by_order_key(torch, order(k0), order(tk), tv)
+
+
+@pytest.mark.parametrize("dtype,n", [
+    (np.uint32, 1 << 30),                       # 1G records: the top of the benchmark's size range
+    (np.uint64, 1 << 30),                       # 8 GiB of keys
+    (np.uint32, binding.MAX_BUCKET_KEYS),       # the largest array the C ABI accepts
+])
+def test_largest_sizes_pairs(dtype, n):
+    """Arrays of 4 to 16 GiB: every byte offset beyond 4 GiB, tile and job
+    counts near the workspace bounds and, for 2^31 - 2 uniform 4-byte keys, a
+    third partition level (level-2 buckets of about 32K keys).  Keys come
+    from the device generator, payloads are the input positions."""
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    tdt = torch.uint32 if dtype == np.uint32 else torch.uint64
+    k0 = torch.empty(n, dtype=tdt, device="cuda")
+    binding.generate(k0, 0x0811_3448 + n)
+    tk = k0.clone()
+    tv = torch.arange(n, dtype=torch.int32, device="cuda")
+    ws = binding.workspace(n, np.dtype(dtype).itemsize, 4)
+    binding.sort_pairs(tk, tv, ws=ws)
+    binding.check_status(ws)
+    del ws
+    _check_stable_sort(torch, k0, tk, tv)
+    del k0, tk, tv
+    torch.cuda.empty_cache()
+
+
+def test_billion_keys_only_u32():
+    require_gpu()
+    torch = pytest.importorskip("torch")
+    n = 1 << 30
+    k0 = torch.empty(n, dtype=torch.uint32, device="cuda")
+    binding.generate(k0, 0x3448_0811)
+    tk = k0.clone()
+    ws = binding.workspace(n, 4, 0)
+    binding.sort_keys(tk, ws=ws)
+    binding.check_status(ws)
+    del ws
+    k = tk.to(torch.int64)
+    del tk
+    ref = torch.sort(k0.to(torch.int64)).values
+    assert bool((ref == k).all())
+    del k0, k, ref
+    torch.cuda.empty_cache()
