@@ -73,8 +73,9 @@ typedef enum {
  * defaults. */
 typedef struct {
     int tile_keys;          /* keys per partition tile: 0 or the width's tile --
-                               6144 (4-byte keys), 4096 (8-byte keys), 2048
-                               (16-byte keys) */
+                               6144 (4-byte keys with a payload), 7168 (4-byte
+                               keys alone), 4096 (8-byte keys), 2048 (16-byte
+                               keys) */
     int bits_per_pass;      /* k, key bits consumed per partition pass: 0 or 8 */
     int small_cutoff;       /* C: buckets of <= C keys are finished in shared memory;
                                2048 .. the finisher capacity for the key/payload size */
@@ -150,8 +151,9 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
  * memory through a fixed pool with a hard budget, or a latency-critical loop
  * that must not call (and synchronise on) cudaMalloc.
  *   Arguments, layout and results as binar_partition_pass.
- *   Limit: n <= 25,006,079 keys of 4 bytes, 16,670,719 of 8 bytes,
- *   8,335,359 of 16 bytes (the look-back state of one pass in 4 MiB);
+ *   Limit: n <= 29,173,759 keys of 4 bytes alone, 25,006,079 of 4 bytes
+ *   with a payload, 16,670,719 of 8 bytes, 8,335,359 of 16 bytes (the
+ *   look-back state of one pass in 4 MiB);
  *   larger n returns BINAR_ERR_WORKSPACE_TOO_SMALL before any work.
  *   The first call on a device looks up the scratch array's device address
  *   (host-side set-up); make that first call before any stream capture.

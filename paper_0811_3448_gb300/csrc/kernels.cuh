@@ -26,15 +26,16 @@ template <int KB> struct TileShape {
     static constexpr int kTile = kThreads * kItems;
 };
 // Items per thread of a partition / histogram tile -- 6144 keys for 4-byte
-// keys, 4096 for 8-byte keys, 2048 for 16-byte keys -- and the resident
-// partition CTAs per SM the register budget is sized for: 3 (measured against
-// 4096 / 2048-key tiles at 4 CTAs/SM, the larger tiles spread the per-tile
-// ticket, scan and look-back over more keys), 4 for keys without payload,
-// whose tiles leave room for a fourth CTA (measured faster despite a few
-// spilled registers).  Every kernel of a call uses the same tile
-// (Params::tile).
+// keys with a payload, 7168 for 4-byte keys alone, 4096 for 8-byte keys, 2048
+// for 16-byte keys -- and the resident partition CTAs per SM the register
+// budget is sized for: 3 (measured against 4096 / 2048-key tiles at 4 CTAs/SM,
+// the larger tiles spread the per-tile ticket, scan and look-back over more
+// keys), 4 for keys without payload, whose tiles leave room for a fourth CTA
+// (measured faster despite a few spilled registers; for 4-byte keys alone,
+// 7168-key tiles measured faster than 3072 / 4096 at 5-8 CTAs/SM and than
+// 6144 / 8192 at 4).  Every kernel of a call uses the same tile (Params::tile).
 template <int KB, int VB> struct PartShape {
-    static constexpr int kItems = KB == 4 ? 24 : (KB == 8 ? 16 : 8);
+    static constexpr int kItems = KB == 4 ? (VB == 0 ? 28 : 24) : (KB == 8 ? 16 : 8);
     static constexpr int kTile = kThreads * kItems;
     static constexpr int kMinBlocks = (VB == 0 && KB != 16) ? 4 : 3;
 };

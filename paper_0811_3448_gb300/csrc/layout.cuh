@@ -49,9 +49,11 @@ int launch(const char *name, int index, cudaStream_t s, F &&f) {
 // ---------------------------------------------------------------------------
 constexpr int kMinCutoff = 2048;
 
-// keys per partition tile, and the finisher's largest job (= the largest cutoff)
-// keys per partition tile (kernels.cuh PartShape)
-inline int tile_for(int kb, int /*vb*/) { return kb == 4 ? 6144 : (kb == 8 ? 4096 : 2048); }
+// keys per partition tile (kernels.cuh PartShape), and the finisher's largest
+// job (= the largest cutoff)
+inline int tile_for(int kb, int vb) {
+    return kb == 4 ? (vb == 0 ? 7168 : 6144) : (kb == 8 ? 4096 : 2048);
+}
 inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
 inline int levels_for(int kb) { return 8 * kb / kBits; }
 

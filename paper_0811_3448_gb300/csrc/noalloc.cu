@@ -25,8 +25,9 @@ namespace {
 
 // 4 MiB per GPU that loads the library, held until the process exits.  It
 // covers the look-back cells, tile map, histograms and counters of one pass
-// over up to 25,006,079 keys of 4 bytes, 16,670,719 of 8 bytes or 8,335,359
-// of 16 bytes (one 1 KB cell row per tile of 6144 / 4096 / 2048 keys).
+// over up to 29,173,759 keys of 4 bytes alone, 25,006,079 of 4 bytes with a
+// payload, 16,670,719 of 8 bytes or 8,335,359 of 16 bytes (one 1 KB cell row
+// per tile of 7168 / 6144 / 4096 / 2048 keys).
 constexpr size_t kScratchBytes = 4u << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 

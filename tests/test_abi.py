@@ -93,8 +93,9 @@ def test_argument_checks_need_no_gpu(lib):
     cfg = binding.Config(bits_per_pass=5)
     assert _call_keys(lib, aligned, 10, 4, 0, aligned, big, ctypes.byref(cfg)) == \
         binding.ERR_UNSUPPORTED
-    # a tile other than the key width's (6144 / 4096 / 2048 keys) is not compiled
-    for kb, wrong in ((4, 4096), (4, 3072), (8, 2048), (8, 3072), (16, 4096)):
+    # a tile other than the widths' (7168 for 4-byte keys alone, 4096 / 2048 for
+    # 8 / 16-byte keys) is not compiled
+    for kb, wrong in ((4, 6144), (4, 4096), (4, 3072), (8, 2048), (8, 3072), (16, 4096)):
         cfg = binding.Config(tile_keys=wrong)
         assert _call_keys(lib, aligned, 10, kb, 0, aligned, big, ctypes.byref(cfg)) == \
             binding.ERR_UNSUPPORTED
