@@ -19,6 +19,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -96,11 +97,19 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources' code: comments and whitespace are dropped,
+    so that a comment edit does not mark recorded counters as stale."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0811_3448_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        if not name.endswith((".cu", ".cuh", ".h")):
+            continue
+        with open(os.path.join(csrc, name)) as f:
+            code = f.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(name.encode())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -322,7 +322,8 @@ __device__ __forceinline__ void rank_tile(Packed<ITEMS> &pk, int iu, int len, Ra
     rank_unstable<ITEMS>(pk, iu, len, s);
 }
 
-// cp.async copies of 4 or 8 bytes from global to shared memory (no registers).
+// cp.async copies of 4, 8 or 16 bytes from global to shared memory (no
+// registers), for the LSD finisher.
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -1227,7 +1228,8 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
 // ---------------------------------------------------------------------------
 // finish: one small bucket (job) per ticket, sorted inside shared memory on
 // bits pos .. w-1 -- the rest of the recursion for that sub-array.  Keys and
-// payloads are staged in shared memory with cp.async.
+// payloads are staged in shared memory by the bulk-copy engine (one
+// cp.async.bulk per array, completing on an mbarrier).
 //
 // Fast path: bits above the first bit f where the job's keys differ are equal
 // (AND / OR of the encoded keys), so one MSD split on the 12 bits at f leaves
