@@ -29,7 +29,8 @@
  * (byte 0 most significant).  Payloads ("records", Sorting Formalism) are vb
  * opaque bytes per key and move with their key.
  *
- * Bit numbering follows the paper's listing: position 0 is the most significant
+ * Bit numbering follows the paper's bit extraction (a shift left by the position,
+ * then a test of the top bit): position 0 is the most significant
  * bit of the encoding, and a sort over w bits looks at positions 0 .. w-1 (the
  * worked example uses w = 4 on nybbles stored in the high half of a byte).
  *
@@ -140,49 +141,66 @@ static void trace_state(records *r, int pos, int64_t lower, int64_t upper,
 }
 
 /* --------------------------------------------------------------------------
- * Binar sort ("Operation of Algorithm").  The four steps, in the paper's order:
- *   1. base case: stop when the bit positions are used up or the sub-array
- *      holds at most one element;
- *   2. initialise the working bounds lo/hi from the passed bounds lower/upper;
- *   3. partition: extract bit `pos` of the element at the lower working bound;
- *      a zero leaves it in the lower sub-array (lo moves up), a one exchanges it
- *      with the element at the upper working bound (hi moves down); repeat until
- *      the bounds cross;
- *   4. recursive call: if one of the two sub-arrays is empty the array passed
- *      through undivided and is partitioned again on the next bit; otherwise
- *      the lower sub-array [lower, lo-1] and the upper one [lo, upper] are each
- *      partitioned on the next bit.
- * Indices are signed 64-bit so that hi may step below lower without wrapping.
+ * Binar sort ("Operation of Algorithm"), run as iteration over a worklist of
+ * pending sub-arrays ("Algorithm Variants": the recursion replaced by
+ * iteration).  Each pending entry is one call of the method: a sub-array
+ * [lower, upper] and the bit position to split it on.  For each entry the four
+ * steps are taken in the paper's order:
+ *   1. base case ("Evaluate for Recursive Base Case"): nothing to do when the
+ *      bit positions are used up or the sub-array holds at most one element;
+ *   2. bounds ("Initialize Starting Array Bounds"): the lower sub-array starts
+ *      empty at `lower`, the upper sub-array starts empty above `upper`;
+ *   3. partition ("Partition Array into Sub-arrays"): the working element is
+ *      the first one not yet placed; its bit at `pos` is extracted; a zero
+ *      extends the lower sub-array over it, a one exchanges it with the last
+ *      unplaced element and extends the upper sub-array downwards over that
+ *      slot; this repeats until no unplaced element is left;
+ *   4. continuation ("Determine Recursive Call on Sub-arrays"): if either
+ *      sub-array is empty the range passes through undivided to bit pos + 1;
+ *      otherwise both sub-arrays are split on bit pos + 1, the lower one first.
+ * The worklist is a stack, so the lower sub-array and everything below it is
+ * finished before the upper one starts: the order of the recursive method.
+ * The stack never holds more than w + 1 entries (each split adds one).
  * ------------------------------------------------------------------------ */
-static void binar(records *r, int64_t lower, int64_t upper, int pos)
+typedef struct { int64_t lower, upper; int pos; } pending;
+
+static void binar(records *r, int64_t first, int64_t last, int pos0)
 {
-    /* step 1 */
-    if (pos >= r->w || upper - lower + 1 <= 1) return;
+    pending stack[8 * 16 + 2];
+    int top = 0;
+    stack[top++] = (pending){first, last, pos0};
+    while (top > 0) {
+        const pending call = stack[--top];
+        const int64_t lower = call.lower, upper = call.upper;
+        const int pos = call.pos;
 
-    /* step 2 */
-    int64_t lo = lower, hi = upper;
-    trace_state(r, pos, lower, upper, lo, hi);
+        /* step 1 */
+        if (pos >= r->w || upper - lower < 1) continue;
 
-    /* step 3 */
-    while (lo <= hi) {
-        r->visits++;
-        if (bit_of(r, lo, pos) == 0) {
-            lo = lo + 1;
-        } else {
-            exchange(r, lo, hi);
-            hi = hi - 1;
+        /* step 2: [lower, below) is the lower sub-array, [above, upper] the
+         * upper one; the elements in [below, above) are not placed yet */
+        int64_t below = lower, above = upper + 1;
+        trace_state(r, pos, lower, upper, below, above - 1);
+
+        /* step 3 */
+        while (below < above) {
+            r->visits++;
+            if (bit_of(r, below, pos)) {
+                above--;
+                exchange(r, below, above);
+            } else {
+                below++;
+            }
+            trace_state(r, pos, lower, upper, below, above - 1);
         }
-        trace_state(r, pos, lower, upper, lo, hi);
-    }
 
-    /* step 4 */
-    int lower_empty = (lo == lower);
-    int upper_empty = (lo == upper + 1);
-    if (lower_empty || upper_empty) {
-        binar(r, lower, upper, pos + 1);            /* pass-through */
-    } else {
-        binar(r, lower, lo - 1, pos + 1);
-        binar(r, lo, upper, pos + 1);
+        /* step 4 (below == above: the split point) */
+        if (below == lower || below == upper + 1) {
+            stack[top++] = (pending){lower, upper, pos + 1};      /* pass-through */
+        } else {
+            stack[top++] = (pending){below, upper, pos + 1};      /* upper, taken second */
+            stack[top++] = (pending){lower, below - 1, pos + 1};  /* lower, taken first */
+        }
     }
 }
 

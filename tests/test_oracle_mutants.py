@@ -19,8 +19,8 @@ from paper_0811_3448_gb300 import inputs
 SRC = os.path.join(os.path.dirname(oracle.__file__), "binar_oracle.c")
 
 MUTANTS = {
-    "loop_bound": ("while (lo <= hi) {", "while (lo < hi) {"),
-    "dropped_exchange": ("exchange(r, lo, hi);\n            hi = hi - 1;", "hi = hi - 1;"),
+    "loop_bound": ("while (below < above) {", "while (below + 1 < above) {"),
+    "dropped_exchange": ("above--;\n                exchange(r, below, above);", "above--;"),
     "float_negatives": ("if (negative) b = !b;", "if (0) b = !b;"),
     "signed_bit": ("if (map == MAP_SIGNED) {\n        if (pos == 0) b = !b;",
                    "if (map == MAP_SIGNED) {\n        if (pos == 1) b = !b;"),
@@ -28,7 +28,10 @@ MUTANTS = {
                         "for (int pos = 0; pos < w; pos++) {"),
     "digit_weight": ("d = 2 * d + b;\n        }\n        digit[i] = d;",
                      "d = d + b;\n        }\n        digit[i] = d;"),
-    "upper_recursion": ("binar(r, lo, upper, pos + 1);", "binar(r, lo, upper, pos + 2);"),
+    "upper_recursion": ("(pending){below, upper, pos + 1}", "(pending){below, upper, pos + 2}"),
+    "parallel_group_bits": ("g = 2 * g + key_bit(keys + i * kb, kb, map, p);", "g = 2 * g;"),
+    "parallel_start_bit": ("jobs[g].pos = b;", "jobs[g].pos = b + 1;"),
+    "parallel_group_bounds": ("jobs[g].upper = count[g + 1] - 1;", "jobs[g].upper = count[g + 1] - 2;"),
 }
 
 
@@ -68,6 +71,13 @@ def _pins_pass(lib) -> bool:
         ko, vo, offs = oracle.partition_pass(k, v, pos=4, k=8)
         digit = (k >> np.uint32(20)) & np.uint32(255)
         if not np.array_equal(vo, v[np.argsort(digit, kind="stable")]):
+            return False
+        # the parallel variant against np.sort, payload pointing at its key
+        k = inputs.uniform_keys(5000, np.uint32, np.random.Generator(np.random.PCG64(2)))
+        v = inputs.index_payload(5000)
+        k2, v2 = k.copy(), v.copy()
+        oracle.binar_sort_parallel(k2, v2, log2_groups=4)
+        if not (np.array_equal(k2, np.sort(k)) and np.array_equal(k[v2], k2)):
             return False
         return True
     finally:

@@ -243,3 +243,59 @@ def test_occurrence_finds_the_jth_copy():
     five = np.array([5], dtype=np.uint32)
     assert [oracle.occurrence(keys, five, j) for j in range(4)] == [0, 2, 3, -1]
     assert oracle.occurrence(keys, np.array([1], dtype=np.uint32), 0) == 4
+
+
+# ------------------------------------------------------------- parallel variant
+@pytest.mark.parametrize("dtype,key_map,dist", [
+    (np.uint32, MAP_UNSIGNED, "uniform"), (np.uint32, MAP_UNSIGNED, "zipf"),
+    (np.uint32, MAP_UNSIGNED, "distinct8"), (np.uint32, MAP_UNSIGNED, "sorted"),
+    (np.uint64, MAP_UNSIGNED, "uniform"), (np.uint64, MAP_UNSIGNED, "reverse"),
+    (np.int64, MAP_SIGNED, None), (np.float32, MAP_FLOAT, None), ("b16", MAP_BYTES_BE, None)])
+@pytest.mark.parametrize("log2_groups", [0, 1, 4, 8])
+def test_parallel_variant_sorts(dtype, key_map, dist, log2_groups):
+    """The parallel variant ("Algorithm Variants": group p holds the elements
+    whose leading bits spell p, each group sorted on its own) gives the keys of
+    np.sort / sorted(bytes), carries every payload with its key, and places each
+    element at most once per bit plus once for the grouping pass
+    ("Performance Time Analysis": one access per bit per element)."""
+    n = 6000
+    if dist is not None:
+        keys = inputs.config2_keys(n, dtype, dist)
+    elif dtype == np.float32:
+        keys = inputs.config3_f32(n)
+    elif dtype == np.int64:
+        keys = inputs.config3_i64(n)
+    else:
+        keys = inputs.config3_bytes16(n)
+        keys[::5, :12] = keys[0, :12]
+    vals = inputs.index_payload(n)
+    k, v = keys.copy(), vals.copy()
+    visits = oracle.binar_sort_parallel(k, v, key_map=key_map, log2_groups=log2_groups)
+    if keys.ndim == 2:
+        assert [bytes(r) for r in k] == sorted(bytes(r) for r in keys)
+        assert np.array_equal(keys[v.astype(np.int64)], k)
+        w = 128
+    else:
+        expect = np.sort(keys)
+        if dtype == np.float32:   # NaN-free input; -0 and +0 compare equal in numpy
+            assert np.all(k[1:] >= k[:-1])
+            assert np.array_equal(np.sort(k), expect)
+        else:
+            assert np.array_equal(k, expect)
+        assert np.array_equal(keys[v.astype(np.int64)].view(np.uint8), k.view(np.uint8))
+        w = 8 * keys.dtype.itemsize
+    assert np.array_equal(np.sort(v), vals)
+    assert visits <= (w + 1) * n
+
+
+def test_parallel_variant_agrees_with_binar_sort_on_keys():
+    """Both give the unique nondecreasing arrangement, so their keys agree bit
+    for bit, whatever the split width (edge cases: n = 0, 1, all equal)."""
+    for n in (0, 1, 2, 257):
+        for fill in (None, 7):
+            keys = (np.full(n, fill, dtype=np.uint32) if fill is not None else
+                    inputs.uniform_keys(n, np.uint32, np.random.Generator(np.random.PCG64(n))))
+            a, b = keys.copy(), keys.copy()
+            oracle.binar_sort(a)
+            oracle.binar_sort_parallel(b, log2_groups=3)
+            assert np.array_equal(a, b)
