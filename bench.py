@@ -196,12 +196,23 @@ def cpu_baseline(n_sample: int, dist: str, kdt=np.uint32):
     log2g = max(0, int(math.floor(math.log2(cores))))
     keys = inputs.config2_keys(n_sample, kdt, dist)
     vals = inputs.index_payload(n_sample)
+    k = keys.copy()
     t0 = time.perf_counter()
-    oracle.binar_sort_parallel(keys, vals, log2_groups=log2g)
+    oracle.binar_sort_parallel(k, vals, log2_groups=log2g)
     dt = time.perf_counter() - t0
     return {"value": n_sample / dt / 1e9, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
             "sample": f"{n_sample} {np.dtype(kdt).name} keys + uint32 payload ({dist}), parallel binar sort "
-                      f"(leading-bit split, one thread per group), {dt:.2f} s wall"}
+                      f"(leading-bit split, one thread per group), {dt:.2f} s wall",
+            "validated": host_sorted_pairs(keys, k, vals)}
+
+
+def host_sorted_pairs(orig: np.ndarray, keys: np.ndarray, vals: np.ndarray) -> bool:
+    """A CPU sort's output is nondecreasing and every payload (the original
+    index) points at the key it travels with, each index once."""
+    ok = bool(np.all(keys[1:] >= keys[:-1]))
+    idx = vals.astype(np.int64)
+    ok &= bool(np.array_equal(np.sort(idx), np.arange(len(orig), dtype=np.int64)))
+    return ok and bool(np.array_equal(orig[idx], keys))
 
 
 def max_over_ranks(ms: float, dist, device) -> float:
@@ -243,12 +254,15 @@ def run_reference(args):
     keys = inputs.config2_keys(n, kdt, args.dist)
     vals = inputs.index_payload(n)
     times = []
+    valid = True
     for i in range(args.warmup + args.steps):
         kk, vv = keys.copy(), vals.copy()
         t0 = time.perf_counter()
         oracle.binar_sort_parallel(kk, vv, log2_groups=log2g)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
+        if i == 0 or i == args.warmup + args.steps - 1:
+            valid &= host_sorted_pairs(keys, kk, vv)
     ms = 1e3 * statistics.mean(times)
     value = n / (ms * 1e-3) / 1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
@@ -259,7 +273,9 @@ def run_reference(args):
                       "parallelism": "replicas"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
                             "sample": f"{n} keys per step (bounded sample of the {args.n}-key "
-                                      f"workload), parallel binar sort on host cores"},
+                                      f"workload), parallel binar sort on host cores",
+                            "validated": valid},
+           "validated": valid,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -312,6 +328,50 @@ def keys_only_partition_roofline(binding, torch, keys0, keys, kb, n, peak, peak_
             "algorithmic_bytes_per_launch": alg, "frac_of_8TBs_spec": achieved / 8000.0,
             "ms_per_launch": per_launch_ms, "sort_ms": total,
             "sort_gkeys_per_s": n / (total * 1e-3) / 1e9, "validated": ok}
+
+
+def small_sort(binding, torch, dev, n: int = 1 << 20, reps: int = 50):
+    """The 1,048,576 uniform uint32 keys of the small configuration, sorted by
+    binar_sort_keys (32 bit levels): 4 MiB, resident in L2 and bound by launch
+    latency, so its roofline fraction is not meaningful.  Timed per call with
+    CUDA events, as stream launches and as one CUDA-graph replay of the call."""
+    from paper_0811_3448_gb300 import inputs
+    keys_h = inputs.config1_keys(n)
+    k0 = torch.from_numpy(keys_h).to(dev)
+    k = torch.empty_like(k0)
+    ws = binding.workspace(n, 4, 0, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(run):
+        ts = []
+        for i in range(reps + 3):
+            k.copy_(k0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    ms = timed(lambda: binding.sort_keys(k, ws=ws))
+    binding.check_status(ws)
+    ok = bool(torch.equal(k.cpu(), torch.from_numpy(np.sort(keys_h))))
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            binding.sort_keys(k, ws=ws)
+    stream.wait_stream(cap)
+    gms = timed(graph.replay)
+    binding.check_status(ws)
+    ok &= bool(torch.equal(k.cpu(), torch.from_numpy(np.sort(keys_h))))
+    return {"workload": f"{n} uniform uint32 keys, keys only (binar_sort_keys)", "n": n,
+            "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_median": ms,
+            "graph_value": n / (gms * 1e-3) / 1e9, "graph_ms_median": gms,
+            "validated": ok, "l2": "4 MiB input, L2-resident (launch-bound; no roofline)"}
 
 
 def run_e2e(args, binding, torch, dev, keys_h, vals_h, ws, keys, vals, world):
@@ -440,7 +500,6 @@ def run_binar(args):
     barrier()
     sampler.start()
     time.sleep(0.3)
-    binding.profile_start()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         keys.copy_(keys0)
@@ -450,6 +509,17 @@ def run_binar(args):
         evs[i][1].record(stream)
     barrier()
     wall = time.perf_counter() - wall0
+    binding.check_status(ws)
+    # the per-kernel split comes from a second loop of the same sorts with
+    # every launch bracketed by CUDA events on the sort's stream, so that the
+    # timed loop above runs the plain call
+    prof_steps = min(args.steps, 20)
+    binding.profile_start()
+    for i in range(prof_steps):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        binding.sort_pairs(keys, vals, ws=ws)
+    torch.cuda.synchronize()
     kstats = binding.profile_stop()
     sampler.stop()
     binding.check_status(ws)
@@ -484,7 +554,9 @@ def run_binar(args):
     # keys: equal keys are indistinguishable), against 2 K n bytes
     roofline_keys = keys_only_partition_roofline(binding, torch, keys0, keys, kb, n, peak, peak_src,
                                                  steps=min(args.steps, 20))
-    gpu_launches = int(sum(l for l, _ in kstats.values()))
+    launches_per_sort = sum(l for l, _ in kstats.values()) / max(prof_steps, 1)
+    gpu_launches = int(round(launches_per_sort * args.steps))
+    instrumented_ms = sum(t for _, t in kstats.values()) / max(prof_steps, 1)
 
     # end to end through the public API: pinned host buffers, copies inside the timed region
     e2e = run_e2e(args, binding, torch, dev, keys_h, vals_h, ws, keys, vals, world)
@@ -504,7 +576,11 @@ def run_binar(args):
            "e2e": e2e, "roofline": roofline, "gpu_launches": gpu_launches,
            "clocks": sampler.summary(), "validated": valid, "dominant_kernel": dominant,
            "kernels": kernels, "wall_s_timed_loop": wall, "ms_median": ms_median,
-           "roofline_keys_only": roofline_keys}
+           "kernel_split": {"steps": prof_steps, "form": "separate loop, every launch "
+                            "bracketed by CUDA events on the sort's stream",
+                            "sum_of_kernels_ms": instrumented_ms},
+           "roofline_keys_only": roofline_keys,
+           "config1": small_sort(binding, torch, dev)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(32 << 20, args.dist, kdt)
     print(json.dumps(out), flush=True)
