@@ -159,12 +159,22 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
  *   (host-side set-up); make that first call before any stream capture.
  *   Every call shares the one scratch array and each call resets what it
  *   needs, so calls that overlap on the GPU (different streams, or threads)
- *   race and must not be issued.  Device-side errors are recorded in the
- *   shared scratch only; they are not readable by the caller. */
+ *   race and must not be issued.  Device-side errors (a wait past its time
+ *   limit, an index outside its range) are recorded in the shared scratch and
+ *   read with binar_partition_pass_noalloc_status(). */
 int binar_partition_pass_noalloc(const void *d_keys_in, const void *d_vals_in, void *d_keys_out,
                                  void *d_vals_out, int64_t n, int key_bytes, binar_key_map map,
                                  int val_bytes, int pos, int bits, int64_t *d_offsets,
                                  void *stream);
+
+/* Status of the most recent binar_partition_pass_noalloc call on this
+ * device (each call clears the word when its first kernel runs): waits for
+ * `stream`, then reads the status word in the library's scratch array into
+ * *out_status (a binar_status, BINAR_OK if no kernel of that call reported an
+ * error) and clears it.  Like the pass itself it
+ * allocates nothing (the word moves through a host variable).  The paper has
+ * no counterpart.  Returns binar_status of the query itself. */
+int binar_partition_pass_noalloc_status(void *stream, int *out_status);
 
 /* Waits for `stream`, then reads the device status word of the workspace
  * into *out_status (a binar_status) and clears it.  Returns binar_status of

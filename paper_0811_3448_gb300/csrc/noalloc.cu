@@ -149,3 +149,25 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     default: return run_call_k16(c);
     }
 }
+
+// The first word of the scratch array is the status word of the pass (the
+// Counters header sits at offset 0 of the layout): read it after the
+// caller's stream has drained, then clear it.  Copies to and from a host
+// variable; nothing is allocated.
+extern "C" int binar_partition_pass_noalloc_status(void *stream, int *out_status) {
+    if (!out_status) return BINAR_ERR_INVALID_ARG;
+    void *scratch = nullptr;
+    int rc = scratch_address(&scratch);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, scratch, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return BINAR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BINAR_ERR_CUDA;
+    const uint32_t zero = 0;
+    if (cudaMemcpyAsync(scratch, &zero, sizeof(zero), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return BINAR_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BINAR_ERR_CUDA;
+    *out_status = (int)v;
+    return BINAR_OK;
+}

@@ -287,6 +287,13 @@ class Server:
         try:
             self._enqueue(b)
         except Exception as e:    # the batch fails; its slot and memory come back
+            # work the batch already enqueued on its stream (inputs generated
+            # into its block, the offsets copy from the slot's pinned staging
+            # buffer) must finish before the block and the slot are reused
+            try:
+                self.streams[b.slot].synchronize()
+            except Exception:
+                pass
             for r in b.requests:
                 r.status = "failed"
                 r.error = f"launch: {e}"

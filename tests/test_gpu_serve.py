@@ -122,10 +122,21 @@ def test_failed_launch_releases_its_slot_and_memory(monkeypatch):
     def flaky(*a, **k):
         calls["n"] += 1
         if calls["n"] == 3:
+            # the batch's inputs are still being written on its stream (a
+            # bounded spin stands in for a slow producer) when the launch fails
+            torch.cuda._sleep(20_000_000)
             raise binding.BinarError(binding.ERR_INVALID_ARG, "test")
         return real(*a, **k)
     monkeypatch.setattr(binding, "sort_keys", flaky)
+    real_release = srv.sched.release
+    drained = []
+
+    def release(b):   # a block comes back only once its stream has no work left
+        drained.append(srv.streams[b.slot].query())
+        real_release(b)
+    monkeypatch.setattr(srv.sched, "release", release)
     st = srv.run(reqs, keep=lambda r: True, max_wall_s=60)
+    assert drained and all(drained)
     assert st["failed"] == 1 and st["done"] == 5 and st["failed_launches"] == 1
     assert srv.arena.used == 0 and srv.free_slots == [0]
     failed = [r for r in reqs if r.status == "failed"]
