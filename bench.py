@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--span-log2", type=int, default=16,
                     help="serve: request sizes floor(2^(10 + span U)) keys (16: 1K..64M)")
     ap.add_argument("--slots", type=int, default=4, help="serve: batches in flight")
+    ap.add_argument("--linger-us", type=float, default=0.0,
+                    help="serve: a small batch waits up to this long for more requests "
+                         "of its class while other batches run")
     ap.add_argument("--plain-slots", type=int, default=0,
                     help="serve: stream slots of the one-request-per-launch form (0: --slots)")
     args = ap.parse_args()
@@ -692,7 +695,8 @@ def run_segments(args):
                                   + f" {n} uint32 keys + uint32 payload, one CUDA-graph launch",
                       "segments": segs, "n": n, "parallelism": f"replicas x{world}",
                       "l2": "1 GiB keys + 1 GiB payloads restored before every replay"},
-           "autotuned": {"small_cutoff": cfg.small_cutoff, "ctas_per_sm": cfg.ctas_per_sm,
+           "autotuned": {"tile_keys": cfg.tile_keys, "bits_per_pass": cfg.bits_per_pass,
+                         "small_cutoff": cfg.small_cutoff, "candidates": len(timings),
                          "timings_ms": timings},
            "plain_per_segment": plain, "validated": valid,
            "clocks": sampler.summary()}

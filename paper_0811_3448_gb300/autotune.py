@@ -1,8 +1,11 @@
 """Autotuner for libbinar's tunable parameters.
 
-The knobs are those of ``binar_config``: the small-bucket cutoff C, the number
-of persistent partition CTAs per SM and the partition tile (keys per tile;
-one compiled choice per key width today).  The tuner times every candidate on
+The knobs are those of ``binar_config``: the partition tile (keys per tile:
+two compiled shapes per key and payload width), the key bits fused per
+partition pass k (6, 7 or 8: fewer bits make more, smaller levels and a
+different bucket-size spread at the finisher) and the small-bucket cutoff C
+(buckets of at most C keys finish in shared memory).  Persistent CTAs per SM
+stay at each kernel's occupancy.  The tuner times every candidate on
 the caller's own data with CUDA events (a few repetitions after a warm-up,
 inputs restored between runs) and keeps the fastest.  Results are cached in a
 JSON file (``$BINAR_TUNE_CACHE`` or ``~/.cache/libbinar/tune.json``) keyed by
@@ -55,11 +58,24 @@ def shape_key(n: int, key_bytes: int, val_bytes: int, num_segments: int = 0,
     return f"{dev}|k{key_bytes}|v{val_bytes}|n2^{max(0, int(math.log2(max(n, 1))))}|s{seg_class}"
 
 
-def candidates(key_bytes: int):
-    """Every (small_cutoff, ctas_per_sm) pair the library accepts for the key width."""
+BITS = (6, 7, 8)
+
+
+def candidates(key_bytes: int, val_bytes: int = 0):
+    """Every (tile, bits per pass, small cutoff) the library accepts for the shape."""
     cap = {4: 8192, 8: 4096, 16: 2048}[key_bytes]
     cutoffs = [c for c in (2048, 4096, 8192) if c <= cap]
-    return [binding.Config(small_cutoff=c, ctas_per_sm=k) for c in cutoffs for k in (0, 1, 2)]
+    return [binding.Config(tile_keys=t, bits_per_pass=b, small_cutoff=c)
+            for t in binding.tile_choices(key_bytes, val_bytes) for b in BITS for c in cutoffs]
+
+
+def describe(cfg) -> str:
+    return f"tile={cfg.tile_keys},bits={cfg.bits_per_pass},cutoff={cfg.small_cutoff}"
+
+
+def _as_dict(cfg) -> dict:
+    return {"tile_keys": cfg.tile_keys, "bits_per_pass": cfg.bits_per_pass,
+            "small_cutoff": cfg.small_cutoff}
 
 
 def _time(run, restore, reps: int = 3) -> float:
@@ -89,7 +105,7 @@ def tune(keys: torch.Tensor, vals: torch.Tensor = None, offsets: torch.Tensor = 
     with _lock:
         cache = _load_cache() if use_cache else {}
         hit = cache.get(key)
-    if hit is not None:
+    if hit is not None and set(hit.get("config", {})) == set(_as_dict(binding.Config())):
         return binding.Config(**hit["config"]), hit.get("timings", {})
     work_k = torch.empty_like(keys)
     work_v = None if vals is None else torch.empty_like(vals)
@@ -101,7 +117,7 @@ def tune(keys: torch.Tensor, vals: torch.Tensor = None, offsets: torch.Tensor = 
             work_v.copy_(vals)
 
     timings, best, best_ms = {}, None, float("inf")
-    for cfg in candidates(kb):
+    for cfg in candidates(kb, vb):
         if offsets is not None:
             run = lambda: binding.sort_segmented(work_k, offsets, work_v, key_map=key_map, ws=ws,
                                                  config=cfg)
@@ -111,12 +127,10 @@ def tune(keys: torch.Tensor, vals: torch.Tensor = None, offsets: torch.Tensor = 
             run = lambda: binding.sort_keys(work_k, key_map=key_map, ws=ws, config=cfg)
         ms = _time(run, restore, reps)
         binding.check_status(ws)
-        desc = f"cutoff={cfg.small_cutoff},ctas_per_sm={cfg.ctas_per_sm}"
-        timings[desc] = ms
+        timings[describe(cfg)] = ms
         if ms < best_ms:
             best, best_ms = cfg, ms
-    entry = {"config": {"small_cutoff": best.small_cutoff, "ctas_per_sm": best.ctas_per_sm},
-             "ms": best_ms, "timings": timings}
+    entry = {"config": _as_dict(best), "ms": best_ms, "timings": timings}
     if use_cache:
         with _lock:
             cache = _load_cache()

@@ -96,6 +96,18 @@ def load():
         return lib
 
 
+# Keys per partition tile of the two compiled tile shapes (binar_config.tile_keys):
+# by key width, and for 4-byte keys by whether a payload moves with them.
+_TILES = {(4, False): (7168, 4096), (4, True): (6144, 4096), (8, False): (4096, 2048),
+          (8, True): (4096, 2048), (16, False): (2048, 1024), (16, True): (2048, 1024)}
+MIN_SORT_BITS, MAX_BITS = 4, 8
+
+
+def tile_choices(key_bytes: int, val_bytes: int = 0):
+    """The tile sizes binar_config.tile_keys accepts for this shape (default first)."""
+    return _TILES[(key_bytes, val_bytes > 0)]
+
+
 # ------------------------------------------------------------------ helpers
 _DEFAULT_MAP = {torch.uint32: MAP_UNSIGNED, torch.uint64: MAP_UNSIGNED,
                 torch.int32: MAP_SIGNED, torch.int64: MAP_SIGNED,
@@ -215,22 +227,21 @@ def sort_segmented(keys: torch.Tensor, offsets: torch.Tensor, vals: torch.Tensor
 
 
 def partition_pass(keys: torch.Tensor, vals: torch.Tensor = None, pos: int = 0, key_map=None,
-                   ws=None, config=None, stream=None, out=None):
-    """One stable 8-bit partition pass at bit ``pos``, out of place.
-
-    Returns (keys_out, vals_out, offsets[257])."""
+                   ws=None, config=None, stream=None, out=None, bits: int = 8):
+    """One stable partition pass on the ``bits`` (1 .. 8) key bits at bit
+    ``pos``, out of place.  Returns (keys_out, vals_out, offsets[2^bits + 1])."""
     _check_dev(keys, vals)
     n, kb, dmap = key_layout(keys)
     vb = _val_bytes(vals)
     if out is None:
         ko = torch.empty_like(keys)
         vo = None if vals is None else torch.empty_like(vals)
-        offs = torch.empty(257, dtype=torch.int64, device=keys.device)
+        offs = torch.empty((1 << bits) + 1, dtype=torch.int64, device=keys.device)
     else:
         ko, vo, offs = out
     ws = _ws_for(ws, n, kb, vb, 1, keys.device)
     _check(load().binar_partition_pass(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), n, kb,
-                                       dmap if key_map is None else key_map, vb, pos, 8,
+                                       dmap if key_map is None else key_map, vb, pos, bits,
                                        _ptr(offs), _ptr(ws), ws.numel(), _cfg(config),
                                        _stream(stream)),
            "binar_partition_pass")

@@ -107,16 +107,27 @@ int check_types(int key_bytes, int map, int val_bytes) {
 }
 
 // Resolves a (nullable) config for the key size into the call.
-int resolve_config(const binar_config *cfg, int key_bytes, int val_bytes, Call &c) {
-    const int T = tile_for(key_bytes, val_bytes);
+// min_bits: the smallest bits per pass the call accepts (a sort bounds its
+// level count by kMinSortBits; a single pass takes any width down to 1).
+int resolve_config(const binar_config *cfg, int key_bytes, int val_bytes, Call &c,
+                   int min_bits = kMinSortBits) {
     const int cap = finish_cap_for(key_bytes);
     c.cutoff = cap;
     c.ctas_per_sm = 0;
     c.timeout_ns = 1000000000LL;
     c.skip_publish_tile = -1;
+    c.bits = kBits;
+    c.tile_variant = 0;
     if (!cfg) return BINAR_OK;
-    if (cfg->tile_keys != 0 && cfg->tile_keys != T) return BINAR_ERR_UNSUPPORTED;
-    if (cfg->bits_per_pass != 0 && cfg->bits_per_pass != kBits) return BINAR_ERR_UNSUPPORTED;
+    if (cfg->tile_keys != 0) {
+        if (cfg->tile_keys == tile_for(key_bytes, val_bytes, 0)) c.tile_variant = 0;
+        else if (cfg->tile_keys == tile_for(key_bytes, val_bytes, 1)) c.tile_variant = 1;
+        else return BINAR_ERR_UNSUPPORTED;
+    }
+    if (cfg->bits_per_pass != 0) {
+        if (cfg->bits_per_pass < min_bits || cfg->bits_per_pass > kBits) return BINAR_ERR_UNSUPPORTED;
+        c.bits = cfg->bits_per_pass;
+    }
     if (cfg->small_cutoff != 0) {
         if (cfg->small_cutoff < kMinCutoff || cfg->small_cutoff > cap) return BINAR_ERR_INVALID_ARG;
         c.cutoff = cfg->small_cutoff;
@@ -221,7 +232,7 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
                          size_t ws_bytes, const binar_config *cfg, void *stream) {
     int rc = check_types(key_bytes, map, val_bytes);
     if (rc) return rc;
-    if (bits != 0 && bits != kBits) return BINAR_ERR_UNSUPPORTED;
+    if (bits < 0 || bits > kBits) return BINAR_ERR_UNSUPPORTED;
     if (n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
     if (pos < 0 || pos >= 8 * key_bytes) return BINAR_ERR_INVALID_ARG;
     if (n > 0 && (!d_keys_in || !d_keys_out || !aligned_to(d_keys_in, key_bytes) ||
@@ -235,11 +246,13 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
     if (ws_bytes < make_layout(n, 1, key_bytes, val_bytes).total)
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
-    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c))) return rc;
+    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c, 1))) return rc;
+    if (bits != 0) c.bits = bits;
+    c.tile_variant = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) {
         if (d_offsets &&
-            cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * (kRadix + 1), s) != cudaSuccess)
+            cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * ((1 << c.bits) + 1), s) != cudaSuccess)
             return BINAR_ERR_CUDA;
         if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) != cudaSuccess) return BINAR_ERR_CUDA;
         return BINAR_OK;

@@ -11,10 +11,14 @@
 namespace binar {
 
 // k: key bits consumed per partition pass.  The paper splits on one bit per
-// pass ("Partition Array into Sub-arrays"); fusing k = 8 bits does the work of
-// eight of its passes in one read and one write of every live key.
+// pass ("Partition Array into Sub-arrays"); fusing k bits does the work of k
+// of its passes in one read and one write of every live key.  k is chosen per
+// call (Params::bits, at most kBits; 8 by default); every digit-indexed array
+// holds kRadix = 2^kBits entries, of which a pass of k bits uses the first 2^k.
+// kBits is also the window of the shared-memory LSD finisher.
 constexpr int kBits = 8;
 constexpr int kRadix = 1 << kBits;
+constexpr int kMinSortBits = 4;      // smallest k a sort accepts (bounds the level count)
 constexpr int kThreads = 256;        // threads of every tile kernel (one per digit)
 constexpr int kWarps = kThreads / 32;
 
@@ -113,7 +117,8 @@ struct Params {
     int cutoff;                    // finisher cutoff C
     long long timeout_ns;
     int skip_publish_tile;         // test hook: level-0 tile that never publishes (-1 = none)
-    int tile;                      // keys per partition tile for this key / payload width
+    int tile;                      // keys per partition tile (the call's tile variant)
+    int bits;                      // k: key bits per partition pass, 1 .. kBits
 };
 
 // ---------------------------------------------------------------------------
@@ -352,6 +357,17 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
 
 __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Programmatic dependent launch: every kernel of a call is launched with the
+// programmatic-serialization attribute, so the next kernel in the stream may be
+// scheduled while this one drains.  Its first act is to wait until its
+// predecessor has completed and that grid's writes are visible
+// (griddepcontrol.wait); it then allows its own successor to launch.  Nothing
+// is read or written before the wait.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ void set_status(Counters *c, uint32_t code) {

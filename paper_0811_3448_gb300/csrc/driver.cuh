@@ -12,17 +12,17 @@
 
 namespace binar {
 
-template <int KB, int VB, bool STABLE>
+template <int KB, int VB, bool STABLE, int TV>
 int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int level,
                      void *k0, void *k1, void *v0, void *v1) {
-    auto kfn = p.map == BINAR_MAP_UNSIGNED ? k_partition<KB, VB, STABLE, true>
-                                           : k_partition<KB, VB, STABLE, false>;
-    const size_t smem = sizeof(PartitionSmem<KB, VB, STABLE>);
+    auto kfn = p.map == BINAR_MAP_UNSIGNED ? k_partition<KB, VB, STABLE, true, TV>
+                                           : k_partition<KB, VB, STABLE, false, TV>;
+    const size_t smem = sizeof(PartitionSmem<KB, VB, STABLE, TV>);
     int occ = kernel_ctas_per_sm((const void *)kfn, smem);
     if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
     const int grid = device_sms() * (occ > 0 ? occ : 1);
     return launch("partition", level, c.stream, [&] {
-        kfn<<<grid, kThreads, smem, c.stream>>>(ws, p, slot, level, k0, k1, v0, v1);
+        launch_pdl(kfn, grid, kThreads, smem, c.stream, ws, p, slot, level, k0, k1, v0, v1);
     });
 }
 
@@ -30,13 +30,17 @@ template <int KB, int VB, int CLS>
 int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1, void *v0,
                         void *v1) {
     constexpr int IU = FinishClasses<KB>::iu(CLS);
+    // a job holds at most min(cutoff, n) keys: larger classes never get one
+    const long long maxjob = c.cutoff < c.n ? c.cutoff : c.n;
+    if (CLS > 0 && (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) >= maxjob)
+        return BINAR_OK;
     // the identity key map is compiled separately for 4- and 8-byte keys
     auto ffn = (KB != 16 && c.map == BINAR_MAP_UNSIGNED) ? k_finish<KB, VB, CLS, KB != 16>
                                                          : k_finish<KB, VB, CLS, false>;
     const size_t smem = sizeof(FinishSmem<KB, VB, IU>);
     const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
     return launch("finish", CLS, c.stream, [&] {
-        ffn<<<device_sms() * (occ > 0 ? occ : 1), kThreads, smem, c.stream>>>(ws, p, k0, k1, v0, v1);
+        launch_pdl(ffn, device_sms() * (occ > 0 ? occ : 1), kThreads, smem, c.stream, ws, p, k0, k1, v0, v1);
     });
 }
 
@@ -50,9 +54,11 @@ int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0
 
 template <int KB, int VB>
 int run_call_vb(const Call &c) {
-    constexpr int T = PartShape<KB, VB>::kTile;
     constexpr int STABLE = VB > 0;
-    const int L = levels_for(KB);
+    const int tv = c.pass_mode ? 0 : c.tile_variant;      // a single pass uses tile shape 0
+    const int T = tv ? PartShape<KB, VB, 1>::kTile : PartShape<KB, VB, 0>::kTile;
+    const int bits = c.bits > 0 ? c.bits : kBits;
+    const int L = levels_for(KB, bits);
     const int sms = device_sms();
     if (sms <= 0) return BINAR_ERR_CUDA;
     const Layout lay = c.layout ? *c.layout : make_layout(c.n, c.offsets ? c.num_segments : 1, KB, VB);
@@ -64,6 +70,7 @@ int run_call_vb(const Call &c) {
     p.timeout_ns = c.timeout_ns;
     p.skip_publish_tile = c.skip_publish_tile;
     p.tile = T;
+    p.bits = bits;
     const int small_grid = sms * 4;
     int rc;
 
@@ -72,25 +79,25 @@ int run_call_vb(const Call &c) {
         p.vals = const_cast<void *>(c.vals_in);
         const uint32_t tiles = (uint32_t)((c.n + T - 1) / T);
         if ((rc = launch("init", -1, c.stream, [&] {
-                 k_init<KB><<<1, 1, 0, c.stream>>>(ws, c.n, 0, c.pass_pos, tiles, 1);
+                 launch_pdl(k_init<KB>, 1, 1, 0, c.stream, ws, c.n, 0, c.pass_pos, tiles, 1);
              })))
             return rc;
-        if ((rc = launch("prep", 0, c.stream, [&] { k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, 0); })))
+        if ((rc = launch("prep", 0, c.stream, [&] { launch_pdl(k_prep, small_grid, kThreads, 0, c.stream, ws, 0); })))
             return rc;
         {
             auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
             const int occ = kernel_ctas_per_sm((const void *)hfn, 0);
             if ((rc = launch("hist", 0, c.stream, [&] {
-                     hfn<<<sms * (occ > 0 ? occ : 1), kThreads, 0, c.stream>>>(ws, p, 0, 0);
+                     launch_pdl(hfn, sms * (occ > 0 ? occ : 1), kThreads, 0, c.stream, ws, p, 0, 0);
                  })))
                 return rc;
         }
         if ((rc = launch("prefix", -1, c.stream, [&] {
-                 k_prefix_only<<<1, kThreads, 0, c.stream>>>(ws, c.pass_offsets, c.n);
+                 launch_pdl(k_prefix_only, 1, kThreads, 0, c.stream, ws, c.pass_offsets, c.n, bits);
              })))
             return rc;
-        return launch_partition<KB, VB, true>(c, ws, p, 0, 1, const_cast<void *>(c.keys_in),
-                                              c.keys_out, const_cast<void *>(c.vals_in), c.vals_out);
+        return launch_partition<KB, VB, true, 0>(c, ws, p, 0, 1, const_cast<void *>(c.keys_in),
+                                                 c.keys_out, const_cast<void *>(c.vals_in), c.vals_out);
     }
 
     p.keys = c.keys;
@@ -99,7 +106,7 @@ int run_call_vb(const Call &c) {
     const bool seg = c.offsets != nullptr;
     const uint32_t tiles0 = (uint32_t)((c.n + T - 1) / T);
     if ((rc = launch("init", -1, c.stream, [&] {
-             k_init<KB><<<1, 1, 0, c.stream>>>(ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
+             launch_pdl(k_init<KB>, 1, 1, 0, c.stream, ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
          })))
         return rc;
     if (seg) {
@@ -108,7 +115,7 @@ int run_call_vb(const Call &c) {
         if (grid > small_grid) grid = small_grid;
         if (grid < 1) grid = 1;
         if ((rc = launch("seed", -1, c.stream, [&] {
-                 k_seed_segments<KB><<<grid, kThreads, 0, c.stream>>>(ws, c.offsets, S, c.n, c.cutoff, T);
+                 launch_pdl(k_seed_segments<KB>, grid, kThreads, 0, c.stream, ws, c.offsets, S, c.n, c.cutoff, T);
              })))
             return rc;
     }
@@ -119,23 +126,25 @@ int run_call_vb(const Call &c) {
         for (int l = 0; l < L; l++) {
             const int slot = l & 1;
             if ((rc = launch("prep", l, c.stream, [&] {
-                     k_prep<<<small_grid, kThreads, 0, c.stream>>>(ws, slot);
+                     launch_pdl(k_prep, small_grid, kThreads, 0, c.stream, ws, slot);
                  })))
                 return rc;
             if ((rc = launch("hist", l, c.stream, [&] {
-                     hfn<<<hgrid, kThreads, 0, c.stream>>>(ws, p, slot, 0);
+                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, 0);
                  })))
                 return rc;
             if ((rc = launch("classify", l, c.stream, [&] {
-                     k_classify<KB><<<small_grid, kThreads, 0, c.stream>>>(ws, p, slot, l == L - 1);
+                     launch_pdl(k_classify<KB>, small_grid, kThreads, 0, c.stream, ws, p, slot, l == L - 1);
                  })))
                 return rc;
-            if ((rc = launch_partition<KB, VB, STABLE>(c, ws, p, slot, l, k0, k1, v0, v1))) return rc;
+            if ((rc = tv ? launch_partition<KB, VB, STABLE, 1>(c, ws, p, slot, l, k0, k1, v0, v1)
+                         : launch_partition<KB, VB, STABLE, 0>(c, ws, p, slot, l, k0, k1, v0, v1)))
+                return rc;
         }
     }
     {
         if ((rc = launch("bin_jobs", -1, c.stream, [&] {
-                 k_bin_jobs<KB><<<small_grid, kThreads, 0, c.stream>>>(ws);
+                 launch_pdl(k_bin_jobs<KB>, small_grid, kThreads, 0, c.stream, ws);
              })))
             return rc;
         if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k1, v0, v1,
@@ -145,12 +154,12 @@ int run_call_vb(const Call &c) {
         const size_t lsmem = sizeof(FinishLsdSmem<KB, VB>);
         const int locc = kernel_ctas_per_sm((const void *)lfn, lsmem);
         if ((rc = launch("finish_lsd", -1, c.stream, [&] {
-                 lfn<<<sms * (locc > 0 ? locc : 1), kThreads, lsmem, c.stream>>>(ws, p, k0, k1, v0, v1);
+                 launch_pdl(lfn, sms * (locc > 0 ? locc : 1), kThreads, lsmem, c.stream, ws, p, k0, k1, v0, v1);
              })))
             return rc;
     }
     return launch("copy", -1, c.stream, [&] {
-        k_copy<KB, VB><<<small_grid, kThreads, 0, c.stream>>>(ws, k0, k1, v0, v1);
+        launch_pdl(k_copy<KB, VB>, small_grid, kThreads, 0, c.stream, ws, T, k0, k1, v0, v1);
     });
 }
 

@@ -34,10 +34,15 @@ template <int KB> struct TileShape {
 // (measured faster despite a few spilled registers; for 4-byte keys alone,
 // 7168-key tiles measured faster than 3072 / 4096 at 5-8 CTAs/SM and than
 // 6144 / 8192 at 4).  Every kernel of a call uses the same tile (Params::tile).
-template <int KB, int VB> struct PartShape {
-    static constexpr int kItems = KB == 4 ? (VB == 0 ? 28 : 24) : (KB == 8 ? 16 : 8);
+// TV selects one of two compiled tile shapes (the autotuner's tile choice):
+// 0 is the shape above, 1 a tile of about two thirds or half its keys at one
+// more resident CTA per SM (cheaper ragged tiles when buckets are small).
+template <int KB, int VB, int TV = 0> struct PartShape {
+    static constexpr int kItems = TV == 0 ? (KB == 4 ? (VB == 0 ? 28 : 24) : (KB == 8 ? 16 : 8))
+                                          : (KB == 4 ? 16 : (KB == 8 ? 8 : 4));
     static constexpr int kTile = kThreads * kItems;
-    static constexpr int kMinBlocks = (VB == 0 && KB != 16) ? 4 : 3;
+    static constexpr int kMinBlocks = TV == 0 ? ((VB == 0 && KB != 16) ? 4 : 3)
+                                              : ((VB == 0 && KB != 16) ? 5 : 4);
 };
 
 // ---------------------------------------------------------------------------
@@ -389,6 +394,7 @@ __device__ __forceinline__ void push_job(const Ws &ws, const Job &j) {
 // ---------------------------------------------------------------------------
 template <int KB>
 __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0, int seed_list) {
+    pdl_entry();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Counters *c = ws.ctr;
     uint32_t *cw = reinterpret_cast<uint32_t *>(c);
@@ -422,6 +428,7 @@ __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0
 template <int KB>
 __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_segments,
                                 long long n, int cutoff, int tile) {
+    pdl_entry();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < num_segments;
          s += stride) {
@@ -467,6 +474,7 @@ __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_s
 // empty list for the next level.
 // ---------------------------------------------------------------------------
 static __global__ void k_prep(Ws ws, int slot) {
+    pdl_entry();
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nb = (uint32_t)alloc, nt = (uint32_t)(alloc >> 32);
@@ -535,6 +543,7 @@ __device__ __forceinline__ typename KeyTraits<KB>::Raw shfl_down_raw(typename Ke
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
 template <int KB, bool IDENT>
 __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
+    pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
@@ -666,7 +675,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
                                 const Bits x = enc(r[q][e]);
                                 a = a & x;
                                 o = o | x;
-                                atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                                atomicAdd(&wh[KT::bits_at(x, bk.pos, p.bits)], 1u);
                             }
                         }
                         continue;
@@ -686,7 +695,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
                             const Bits x = enc(r[q][e]);
                             a = a & x;
                             o = o | x;
-                            atomicAdd(&wh[KT::digit(x, bk.pos)], 1u);
+                            atomicAdd(&wh[KT::bits_at(x, bk.pos, p.bits)], 1u);
                             if (!look) {
                             } else if (e + 1 < PER) {
                                 if (idx + 1 < end_rel) {
@@ -719,6 +728,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
 // ---------------------------------------------------------------------------
 template <int KB>
 __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot, int last_level) {
+    pdl_entry();
     using KT = KeyTraits<KB>;
     using Bits = typename KT::Bits;
     constexpr int W = KT::kW;
@@ -822,7 +832,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
         scount[tid] = cnt;
         sexcl[tid] = excl;
         ws.hist[slot][(size_t)b * kRadix + tid] = excl;
-        const int cpos = bk.pos + kBits;
+        const int cpos = bk.pos + p.bits;
         const int cbuf = bk.buf ^ 1;
         const bool terminal = cpos >= W;
         const bool large = !terminal && cnt > (uint32_t)p.cutoff;
@@ -967,7 +977,10 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
 
 // For binar_partition_pass: exclusive prefix of the single bucket's histogram
 // (kept for the partition kernel) and the caller's group offsets.
-static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long long *offsets, long long n) {
+// The caller's offsets array has 2^bits + 1 entries.
+static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long long *offsets, long long n,
+                                                                int bits) {
+    pdl_entry();
     __shared__ uint32_t scratch[kWarps];
     const int tid = threadIdx.x;
     const uint32_t cnt = ws.hist[0][tid];
@@ -975,8 +988,8 @@ static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long lon
     const uint32_t excl = block_exclusive_scan(cnt, scratch, &total);
     ws.hist[0][tid] = excl;
     if (offsets) {
-        offsets[tid] = excl;
-        if (tid == 0) offsets[kRadix] = n;
+        if (tid < (1 << bits)) offsets[tid] = excl;
+        if (tid == 0) offsets[1 << bits] = n;
     }
 }
 
@@ -998,9 +1011,9 @@ static __global__ void __launch_bounds__(kThreads) k_prefix_only(Ws ws, long lon
 constexpr uint32_t kInclusive = 0x80000000u;
 constexpr int kLookbackWindow = 8;
 
-template <int KB, int VB, bool STABLE>
+template <int KB, int VB, bool STABLE, int TV>
 struct PartitionSmem {
-    static constexpr int T = PartShape<KB, VB>::kTile;
+    static constexpr int T = PartShape<KB, VB, TV>::kTile;
     typename RankSmemFor<STABLE>::T rank;
     int offs[kRadix];          // bucket-relative destination of digit d's run, minus its tile start
     uint32_t next_ticket;
@@ -1095,17 +1108,18 @@ __device__ __forceinline__ uint32_t lookback(const Ws &ws, const Params &p, uint
 }
 
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
-template <int KB, int VB, bool STABLE, bool IDENT>
-__global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
+template <int KB, int VB, bool STABLE, bool IDENT, int TV>
+__global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
     k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
                 void *vals1) {
+    pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int ITEMS = PartShape<KB, VB>::kItems;
-    constexpr int T = PartShape<KB, VB>::kTile;
+    constexpr int ITEMS = PartShape<KB, VB, TV>::kItems;
+    constexpr int T = PartShape<KB, VB, TV>::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE> *>(smem_raw);
+    auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE, TV> *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
@@ -1166,7 +1180,7 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
         for (int j = 0; j < ITEMS; j++) {
             const int i = striped(ITEMS, j);
             k[j] = skeys[ks + i];
-            pk.set_dig(j, i < tlen ? KT::digit(enc(k[j]), bk.pos) : 0u);
+            pk.set_dig(j, i < tlen ? KT::bits_at(enc(k[j]), bk.pos, p.bits) : 0u);
         }
         rank_tile<ITEMS>(pk, ITEMS, tlen, s.rank);
 
@@ -1212,7 +1226,7 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB>::kMinBlocks)
             const int i = r * kThreads + tid;
             if (i < tlen) {
                 const Raw kk = skeys[i];
-                const uint32_t at = (uint32_t)(s.offs[KT::digit(enc(kk), bk.pos)] + i);
+                const uint32_t at = (uint32_t)(s.offs[KT::bits_at(enc(kk), bk.pos, p.bits)] + i);
                 if (at < bk.len) {
                     dst[at] = kk;
                     if (VB) vdst[at] = svals[i];
@@ -1273,6 +1287,7 @@ struct FinishSmem {
 // bin_jobs: the job indices, grouped by size class (classes in order).
 template <int KB>
 __global__ void k_bin_jobs(Ws ws) {
+    pdl_entry();
     if (has_error(ws.ctr)) return;
     constexpr int NC = FinishClasses<KB>::kCount;
     uint32_t base[NC];
@@ -1534,6 +1549,7 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
                                                 ? 4
                                                 : (FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2))
     k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
+    pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
@@ -1637,6 +1653,7 @@ struct FinishLsdSmem {
 template <int KB, int VB>
 __global__ void __launch_bounds__(kThreads, 2)
     k_finish_lsd(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
+    pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
@@ -1774,12 +1791,13 @@ __device__ __forceinline__ void copy_range(E *dst, const E *src, long long count
         dst[i] = src[i];
 }
 
+// T: the call's tile (copy jobs are cut into tiles of the partition's size).
 template <int KB, int VB>
-__global__ void __launch_bounds__(kThreads) k_copy(Ws ws, void *keys0, void *keys1, void *vals0,
-                                                   void *vals1) {
+__global__ void __launch_bounds__(kThreads) k_copy(Ws ws, int T, void *keys0, void *keys1,
+                                                   void *vals0, void *vals1) {
+    pdl_entry();
     using Raw = typename KeyTraits<KB>::Raw;
     using V = typename ValTraits<VB>::T;
-    constexpr int T = PartShape<KB, VB>::kTile;
     __shared__ uint32_t sticket;
     if (has_error(ws.ctr)) return;
     const unsigned long long ca = ws.ctr->copy_alloc;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <string>
+#include <utility>
 
 #include "binar_internal.cuh"
 
@@ -17,6 +18,27 @@ int kernel_ctas_per_sm(const void *fn, size_t smem);         // occupancy (cache
 bool profiling_on();
 void profile_record(const std::string &name, cudaEvent_t a, cudaEvent_t b);
 cudaEvent_t profile_event();
+
+// Enqueues kernel<<<grid, block, smem, s>>>(args...) with programmatic stream
+// serialization: the kernel may be scheduled while its predecessor in the
+// stream drains, and waits for it with griddepcontrol.wait (pdl_entry) before
+// touching memory.  This hides most of the launch latency between the
+// dependent kernels of a call.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Launches `f` (which enqueues one kernel) bracketed by profiling events.
 template <typename F>
@@ -49,13 +71,19 @@ int launch(const char *name, int index, cudaStream_t s, F &&f) {
 // ---------------------------------------------------------------------------
 constexpr int kMinCutoff = 2048;
 
-// keys per partition tile (kernels.cuh PartShape), and the finisher's largest
-// job (= the largest cutoff)
-inline int tile_for(int kb, int vb) {
+// keys per partition tile of tile variant tv (kernels.cuh PartShape), and the
+// finisher's largest job (= the largest cutoff)
+inline int tile_for(int kb, int vb, int tv = 0) {
+    if (tv == 1) return kb == 4 ? 4096 : (kb == 8 ? 2048 : 1024);
     return kb == 4 ? (vb == 0 ? 7168 : 6144) : (kb == 8 ? 4096 : 2048);
 }
+inline int min_tile_for(int kb, int vb) {
+    const int a = tile_for(kb, vb, 0), b = tile_for(kb, vb, 1);
+    return a < b ? a : b;
+}
 inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
-inline int levels_for(int kb) { return 8 * kb / kBits; }
+// partition levels of a sort that consumes `bits` key bits per pass
+inline int levels_for(int kb, int bits = kBits) { return (8 * kb + bits - 1) / bits; }
 
 struct Layout {
     size_t ctr, altk, altv, list[2], hist[2], andor[2], order[2], tilemap, cells, jobs, jobidx, jobs2, copies, total;
@@ -66,7 +94,8 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     Layout L{};
-    const long long T = tile_for(kb, vb), lv = levels_for(kb);
+    // capacities cover every tile variant and every bits per pass a sort accepts
+    const long long T = min_tile_for(kb, vb), lv = levels_for(kb, kMinSortBits);
     const long long m = n / (kMinCutoff + 1) + segs + 2;
     const long long t = n / T + m + 2;
     // jobs of a level: own jobs (>= C/8 keys) and merged runs (two adjacent
@@ -146,6 +175,8 @@ struct Call {
     long long n;
     int map, vb;
     int cutoff;
+    int bits;                      // key bits per partition pass
+    int tile_variant;              // 0 or 1 (PartShape TV)
     int ctas_per_sm;
     long long timeout_ns;
     int skip_publish_tile;

@@ -104,7 +104,7 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return BINAR_ERR_INVALID_ARG;
     if (map < BINAR_MAP_UNSIGNED || map > BINAR_MAP_BYTES_BE) return BINAR_ERR_INVALID_ARG;
     if (map == BINAR_MAP_FLOAT && key_bytes == 16) return BINAR_ERR_UNSUPPORTED;
-    if (bits != 0 && bits != kBits) return BINAR_ERR_UNSUPPORTED;
+    if (bits < 0 || bits > kBits) return BINAR_ERR_UNSUPPORTED;
     if (n < 0 || pos < 0 || pos >= 8 * key_bytes) return BINAR_ERR_INVALID_ARG;
     if (n > 0 && (!d_keys_in || !d_keys_out || !aligned_to(d_keys_in, key_bytes) ||
                   !aligned_to(d_keys_out, key_bytes)))
@@ -121,13 +121,16 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) {
         if (d_offsets &&
-            cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * (kRadix + 1), s) != cudaSuccess)
+            cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * ((1 << (bits ? bits : kBits)) + 1),
+                            s) != cudaSuccess)
             return BINAR_ERR_CUDA;
         return BINAR_OK;
     }
     Call c;
     std::memset(&c, 0, sizeof(c));
     c.cutoff = finish_cap_for(key_bytes);
+    c.bits = bits ? bits : kBits;
+    c.tile_variant = 0;
     c.timeout_ns = 1000000000LL;
     c.skip_publish_tile = -1;
     c.pass_mode = true;

@@ -18,8 +18,12 @@ Structure (one host thread, CUDA streams for overlap):
   at arrival.
 * :class:`Server` -- the device side.  A batch's inputs are written into its
   block (``binar_generate``, standing in for the client's producer), the whole
-  batch is one ``binar_sort_segmented`` call on the slot's stream, and an event
-  marks completion.  Requests that arrive while batches run are admitted as
+  batch is one ``binar_sort_segmented`` call on the slot's stream (a batch of
+  one request is sorted by ``binar_sort_pairs`` / ``binar_sort_keys`` directly,
+  without the offsets copy and the segment seeding), and an event marks
+  completion.  With ``linger_s`` > 0 a batch smaller than ``linger_keys`` waits
+  up to ``linger_s`` after its oldest request arrived, while other batches are
+  in flight, for more requests of its class to join.  Requests that arrive while batches run are admitted as
   slots and memory free up, so batches of different classes overlap on the
   device.  ``mode="plain"`` is the comparison form: one request per launch
   (``binar_sort_pairs`` / ``binar_sort_keys``), same slots and budget.
@@ -222,6 +226,22 @@ class Scheduler:
         starts = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64).tolist()
         return Batch(head.cls, chosen, layout, off, starts)
 
+    def should_linger(self, now: float, linger_s: float, linger_keys: int) -> bool:
+        """True while the next batch would be small (its class holds fewer
+        than ``linger_keys`` queued keys) and its oldest request arrived less
+        than ``linger_s`` ago: waiting lets more requests of the class join."""
+        if self._queued == 0:
+            return False
+        q = min((q for q in self.queues.values() if q), key=lambda q: q[0]._seq)
+        if now - q[0].arrival_s >= linger_s:
+            return False
+        total = 0
+        for r in q:
+            total += r.n
+            if total >= linger_keys:
+                return False
+        return True
+
     def release(self, batch: Batch) -> None:
         self.arena.free(batch.arena_off)
 
@@ -241,13 +261,15 @@ class Server:
 
     def __init__(self, budget_bytes: int = 40 << 30, slots: int = 4, mode: str = "batched",
                  max_batch_keys: int = 256 << 20, max_batch_requests: int = 4096,
-                 device=None, config=None):
+                 device=None, config=None, linger_s: float = 0.0, linger_keys: int = 1 << 20):
         import torch
         from . import binding
         if mode not in ("batched", "plain"):
             raise ValueError(f"unknown mode {mode}")
         self.torch, self.binding = torch, binding
         self.mode = mode
+        self.linger_s = linger_s if mode == "batched" else 0.0
+        self.linger_keys = linger_keys
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
             else torch.device(device)
         self.config = config
@@ -318,7 +340,7 @@ class Server:
                 binding.generate(keys[a:a + r.n], r.seed, stream=s)
                 if vals is not None:
                     torch.arange(r.n, dtype=torch.int32, device=self.device, out=vals[a:a + r.n])
-            if self.mode == "batched":
+            if self.mode == "batched" and len(b.requests) > 1:
                 st = self.staging[b.slot]
                 st[:len(b.starts)] = torch.tensor(b.starts, dtype=torch.int64)
                 offs.copy_(st[:len(b.starts)], non_blocking=True)
@@ -370,6 +392,9 @@ class Server:
                     self._complete(b, time.perf_counter() - t0, keep)
                     progressed = True
             while self.free_slots:
+                if self.linger_s > 0 and self.inflight and \
+                        self.sched.should_linger(now, self.linger_s, self.linger_keys):
+                    break
                 b = self.sched.next_batch()
                 if b is None:
                     break
@@ -458,7 +483,7 @@ def bench_main(args) -> Optional[dict]:
     for mode in ("batched", "plain"):
         reqs = requests_from_mix(mix)
         srv = Server(budget_bytes=budget, slots=slots if mode == "batched" else plain_slots,
-                     mode=mode)
+                     mode=mode, linger_s=getattr(args, "linger_us", 0.0) * 1e-6)
         sample = {r.rid for r in reqs[::max(1, len(reqs) // 16)] if r.n <= (4 << 20)}
         out[mode] = srv.run(reqs, keep=lambda r: r.rid in sample)
         # sampled check: each kept result equals the same request sorted alone
@@ -485,7 +510,8 @@ def bench_main(args) -> Optional[dict]:
             "config": {"workload": f"serving: Poisson arrivals {rate:g}/s for {duration:g} s, "
                                    f"sizes floor(2^(10+{span}U)), key type uniform over "
                                    "{uint32, uint64, float32}, uint32 payload with p=1/2, "
-                                   f"{budget >> 30} GiB budget, {slots} stream slots",
+                                   f"{budget >> 30} GiB budget, {slots} stream slots, "
+                                   f"linger {getattr(args, 'linger_us', 0.0):g} us",
                        "requests": len(mix)},
             "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"],
             "batched": b, "plain_one_request_per_launch": p}

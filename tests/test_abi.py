@@ -90,15 +90,21 @@ def test_argument_checks_need_no_gpu(lib):
     cfg = binding.Config(small_cutoff=100)
     assert _call_keys(lib, aligned, 10, 4, 0, aligned, big, ctypes.byref(cfg)) == \
         binding.ERR_INVALID_ARG
-    cfg = binding.Config(bits_per_pass=5)
-    assert _call_keys(lib, aligned, 10, 4, 0, aligned, big, ctypes.byref(cfg)) == \
-        binding.ERR_UNSUPPORTED
-    # a tile other than the widths' (7168 for 4-byte keys alone, 4096 / 2048 for
-    # 8 / 16-byte keys) is not compiled
-    for kb, wrong in ((4, 6144), (4, 4096), (4, 3072), (8, 2048), (8, 3072), (16, 4096)):
+    for bits in (1, 3, 9):      # a sort takes 4 .. 8 bits per pass
+        cfg = binding.Config(bits_per_pass=bits)
+        assert _call_keys(lib, aligned, 10, 4, 0, aligned, big, ctypes.byref(cfg)) == \
+            binding.ERR_UNSUPPORTED
+    # a tile other than the width's two compiled tiles (7168 / 4096 for 4-byte
+    # keys alone, 4096 / 2048 and 2048 / 1024 for 8- and 16-byte keys) is refused
+    for kb, wrong in ((4, 6144), (4, 3072), (4, 8192), (8, 3072), (8, 1024), (16, 4096),
+                      (16, 512)):
         cfg = binding.Config(tile_keys=wrong)
         assert _call_keys(lib, aligned, 10, kb, 0, aligned, big, ctypes.byref(cfg)) == \
             binding.ERR_UNSUPPORTED
+    for kb, vb in ((4, 0), (4, 4), (8, 0), (8, 8), (16, 4)):
+        assert set(binding.tile_choices(kb, vb)) == \
+            {7168 if (kb, vb) == (4, 0) else 6144 if kb == 4 else 4096 if kb == 8 else 2048,
+             4096 if kb == 4 else 2048 if kb == 8 else 1024}
     # pairs without payload width, segmented without offsets
     assert lib.binar_sort_pairs(aligned, aligned, 10, 4, 0, 0, aligned, big, None, None) == \
         binding.ERR_INVALID_ARG
@@ -107,5 +113,7 @@ def test_argument_checks_need_no_gpu(lib):
     # partition pass: bad bit position / digit width
     assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 32, 8, None,
                                     aligned, big, None, None) == binding.ERR_INVALID_ARG
-    assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 0, 4, None,
+    assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 0, 9, None,
+                                    aligned, big, None, None) == binding.ERR_UNSUPPORTED
+    assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 0, -1, None,
                                     aligned, big, None, None) == binding.ERR_UNSUPPORTED

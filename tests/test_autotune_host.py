@@ -7,14 +7,18 @@ import pytest
 from paper_0811_3448_gb300 import autotune
 
 
-@pytest.mark.parametrize("kb,cutoffs", [(4, {2048, 4096, 8192}), (8, {2048, 4096}), (16, {2048})])
-def test_candidates_cover_the_accepted_space(kb, cutoffs):
-    cands = autotune.candidates(kb)
+@pytest.mark.parametrize("kb,vb,cutoffs,tiles", [
+    (4, 4, {2048, 4096, 8192}, {6144, 4096}), (4, 0, {2048, 4096, 8192}, {7168, 4096}),
+    (8, 4, {2048, 4096}, {4096, 2048}), (16, 0, {2048}, {2048, 1024})])
+def test_candidates_cover_the_accepted_space(kb, vb, cutoffs, tiles):
+    cands = autotune.candidates(kb, vb)
     assert {c.small_cutoff for c in cands} == cutoffs
-    assert {c.ctas_per_sm for c in cands} == {0, 1, 2}
-    assert len(cands) == 3 * len(cutoffs)
-    # every other knob is left at the library default
-    assert all(c.tile_keys == 0 and c.bits_per_pass == 0 for c in cands)
+    assert {c.tile_keys for c in cands} == tiles
+    assert {c.bits_per_pass for c in cands} == {6, 7, 8}
+    assert len(cands) == len(tiles) * 3 * len(cutoffs)
+    assert len({autotune.describe(c) for c in cands}) == len(cands)
+    # CTAs per SM stay at each kernel's occupancy
+    assert all(c.ctas_per_sm == 0 for c in cands)
 
 
 def test_shape_key_classes():
@@ -33,8 +37,8 @@ def test_cache_round_trip(tmp_path, monkeypatch):
     monkeypatch.setenv("BINAR_TUNE_CACHE", str(path))
     assert autotune.cache_path() == str(path)
     assert autotune._load_cache() == {}
-    autotune._store_cache({"x": {"config": {"small_cutoff": 4096, "ctas_per_sm": 0}}})
+    autotune._store_cache({"x": {"config": {"small_cutoff": 4096, "bits_per_pass": 7}}})
     assert json.loads(path.read_text())["x"]["config"]["small_cutoff"] == 4096
-    assert autotune._load_cache()["x"]["config"]["ctas_per_sm"] == 0
+    assert autotune._load_cache()["x"]["config"]["bits_per_pass"] == 7
     path.write_text("not json")
     assert autotune._load_cache() == {}                                    # corrupt cache ignored

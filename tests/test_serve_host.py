@@ -195,3 +195,20 @@ def test_long_backlog_batches_in_constant_time_per_request():
         s.release(b)
     assert order == list(range(200_000))           # oldest first across classes
     assert time.perf_counter() - t0 < 30.0
+
+
+def test_linger_waits_only_for_small_young_batches():
+    """A batch lingers while its class holds fewer than linger_keys queued
+    keys and its oldest request is younger than linger_s; never otherwise."""
+    arena = Arena(1 << 30)
+    sched = Scheduler(arena, fake_ws)
+    assert not sched.should_linger(0.0, 1e-3, 1 << 20)              # nothing queued
+    sched.submit(Request(rid=0, n=1000, key_type="u32", has_payload=False, seed=0,
+                               arrival_s=1.0))
+    assert sched.should_linger(1.0002, 1e-3, 1 << 20)                # small and young
+    assert not sched.should_linger(1.002, 1e-3, 1 << 20)             # waited long enough
+    sched.submit(Request(rid=1, n=2 << 20, key_type="u32", has_payload=False, seed=1,
+                               arrival_s=1.0001))
+    assert not sched.should_linger(1.0002, 1e-3, 1 << 20)            # class already large
+    b = sched.next_batch()
+    assert [r.rid for r in b.requests] == [0, 1]
