@@ -20,6 +20,8 @@ function computes, and the passage of the paper it restates:
 * :func:`stable_radix` -- stable binary LSD radix sort, the record-order oracle
   ("Sorting Formalism" with equal keys kept in input order).
 * :func:`partition_pass` -- one stable k-bit partition at bit position ``pos``.
+* :func:`sort_strings` -- the stable lexicographic order of byte strings of
+  different lengths (a proper prefix first), as a permutation.
 * :func:`rank_of` / :func:`occurrence` -- the output position range of one key
   and the input index of its j-th copy, by definition, for checking sampled
   outputs of sorts too large for the other functions.
@@ -75,6 +77,8 @@ def configure(lib):
     lib.oracle_rank_of.restype = i32
     lib.oracle_occurrence.argtypes = [p, i64, i32, p, i64]
     lib.oracle_occurrence.restype = i64
+    lib.oracle_sort_strings.argtypes = [p, p, i64, p]
+    lib.oracle_sort_strings.restype = i32
     return lib
 
 
@@ -117,6 +121,8 @@ def _offsets(n, offsets):
     if offsets is None:
         offsets = np.array([0, n], dtype=np.int64)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    if len(offsets) < 1 or offsets[0] < 0 or offsets[-1] > n or np.any(np.diff(offsets) < 0):
+        raise ValueError("offsets must be nondecreasing within [0, n]")
     return offsets, len(offsets) - 1
 
 
@@ -214,3 +220,17 @@ def occurrence(keys, probe, j):
     kv, kb = _key_view(keys)
     pr = np.ascontiguousarray(np.asarray(probe)).view(np.uint8).reshape(-1)
     return int(_load().oracle_occurrence(_ptr(kv), kv.shape[0], kb, _ptr(pr), j))
+
+
+def sort_strings(data: np.ndarray, offsets: np.ndarray) -> np.ndarray:
+    """Stable lexicographic order of the strings data[offsets[i]:offsets[i+1]]
+    (unsigned bytes, a proper prefix first): returns uint32 indices."""
+    data = np.ascontiguousarray(data, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = len(offsets) - 1
+    if n < 0 or (n > 0 and (offsets[0] < 0 or offsets[-1] > len(data))):
+        raise ValueError("offsets must lie within the byte buffer")
+    order = np.zeros(max(n, 0), dtype=np.uint32)
+    if _load().oracle_sort_strings(_ptr(data), _ptr(offsets), n, _ptr(order)) != 0:
+        raise ValueError("oracle_sort_strings: bad arguments")
+    return order

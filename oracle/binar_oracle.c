@@ -22,9 +22,11 @@
  *   oracle_partition_pass    one stable split of a range into 2^k sub-arrays by
  *                            k bits at bit position pos (the partition step,
  *                            generalised to k bits as in the parallel variant)
+ *   oracle_sort_strings      the stable lexicographic order of byte strings of
+ *                            different lengths (a proper prefix first)
  *
- * Key layout: n keys of kb bytes each, as raw bytes.  Integer and float keys are
- * little-endian machine words (kb = 1, 2, 4, 8, 16 for integers; 4, 8 for
+ * Key layout: n keys of kb bytes each (kb <= 256), as raw bytes.  Integer and
+ * float keys are little-endian machine words (any kb for integers; 4, 8 for
  * floats).  BYTES_BE keys are byte strings compared as big-endian bit strings
  * (byte 0 most significant).  Payloads ("records", Sorting Formalism) are vb
  * opaque bytes per key and move with their key.
@@ -42,6 +44,7 @@
 #include <pthread.h>
 
 enum { MAP_UNSIGNED = 0, MAP_SIGNED = 1, MAP_FLOAT = 2, MAP_BYTES_BE = 3 };
+enum { KB_MAX = 256 };   /* widest key: 2048 bits */
 
 /* --------------------------------------------------------------------------
  * Encoding ("The Other Universal Property").
@@ -79,7 +82,7 @@ static int key_bit(const uint8_t *key, int kb, int map, int pos)
  * Returns 0, or -1 for an unsupported (kb, map). */
 int oracle_map_keys(const uint8_t *keys, uint8_t *mapped, int64_t n, int kb, int map)
 {
-    if (kb <= 0 || kb > 16) return -1;
+    if (kb <= 0 || kb > KB_MAX) return -1;
     if (map == MAP_FLOAT && kb != 4 && kb != 8) return -1;
     if (map < 0 || map > 3) return -1;
     for (int64_t i = 0; i < n; i++) {
@@ -108,7 +111,7 @@ typedef struct {
 
 static void exchange(records *r, int64_t i, int64_t j)
 {
-    uint8_t t[16];
+    uint8_t t[KB_MAX];
     if (i == j) return;
     memcpy(t, r->keys + i * r->kb, (size_t)r->kb);
     memcpy(r->keys + i * r->kb, r->keys + j * r->kb, (size_t)r->kb);
@@ -160,14 +163,16 @@ static void trace_state(records *r, int pos, int64_t lower, int64_t upper,
  *      otherwise both sub-arrays are split on bit pos + 1, the lower one first.
  * The worklist is a stack, so the lower sub-array and everything below it is
  * finished before the upper one starts: the order of the recursive method.
- * The stack never holds more than w + 1 entries (each split adds one).
+ * The stack never holds more than w + 1 entries (at most one pending upper
+ * sub-array per bit position, plus the entry being taken).
  * ------------------------------------------------------------------------ */
 typedef struct { int64_t lower, upper; int pos; } pending;
 
 static void binar(records *r, int64_t first, int64_t last, int pos0)
 {
-    pending stack[8 * 16 + 2];
+    pending *stack = malloc((size_t)(r->w + 2) * sizeof(pending));
     int top = 0;
+    if (!stack) return;
     stack[top++] = (pending){first, last, pos0};
     while (top > 0) {
         const pending call = stack[--top];
@@ -202,11 +207,12 @@ static void binar(records *r, int64_t first, int64_t last, int pos0)
             stack[top++] = (pending){lower, below - 1, pos + 1};  /* lower, taken first */
         }
     }
+    free(stack);
 }
 
 static int check_args(int64_t n, int kb, int map, int vb, int w)
 {
-    if (n < 0 || kb <= 0 || kb > 16 || vb < 0 || vb > 16) return -1;
+    if (n < 0 || kb <= 0 || kb > KB_MAX || vb < 0 || vb > 16) return -1;
     if (map < 0 || map > 3) return -1;
     if (map == MAP_FLOAT && kb != 4 && kb != 8) return -1;
     if (w < 0 || w > 8 * kb) return -1;
@@ -428,4 +434,55 @@ int64_t oracle_occurrence(const uint8_t *keys, int64_t n, int kb, const uint8_t 
         }
     }
     return -1;
+}
+
+/* --------------------------------------------------------------------------
+ * Byte strings of different lengths ("The Other Universal Property": strings
+ * are sorted by their encoding; "Recursion Analysis": a string costs its
+ * average length in bit passes).  The paper gives no rule for strings of
+ * unequal length; the order used is the plain lexicographic one: the first
+ * differing byte decides (unsigned), and a string that is a proper prefix of
+ * another sorts first.  Equal strings keep their input order (the stable
+ * permutation of "Sorting Formalism").
+ *
+ * oracle_sort_strings writes order[k] = index of the k-th string in that
+ * order, string i being bytes[offsets[i] .. offsets[i+1]).  It is the plain
+ * definition: a merge sort of the indices (stable: on a tie the left run's
+ * element is taken first) with the comparison written out byte by byte.
+ * ------------------------------------------------------------------------ */
+static int compare_strings(const uint8_t *bytes, const int64_t *offsets, uint32_t a, uint32_t b)
+{
+    const int64_t la = offsets[a + 1] - offsets[a], lb = offsets[b + 1] - offsets[b];
+    const uint8_t *sa = bytes + offsets[a], *sb = bytes + offsets[b];
+    const int64_t common = la < lb ? la : lb;
+    for (int64_t i = 0; i < common; i++)
+        if (sa[i] != sb[i]) return sa[i] < sb[i] ? -1 : 1;
+    if (la != lb) return la < lb ? -1 : 1;
+    return 0;
+}
+
+int oracle_sort_strings(const uint8_t *bytes, const int64_t *offsets, int64_t n, uint32_t *order)
+{
+    if (n < 0 || n > 0xFFFFFFFFLL) return -1;
+    for (int64_t i = 0; i < n; i++)
+        if (offsets[i + 1] < offsets[i] || offsets[i] < 0) return -1;
+    uint32_t *tmp = malloc((size_t)(n + 1) * sizeof(uint32_t));
+    if (!tmp) return -1;
+    for (int64_t i = 0; i < n; i++) order[i] = (uint32_t)i;
+    /* bottom-up merge sort: runs of width 1, 2, 4, ... */
+    for (int64_t width = 1; width < n; width *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * width) {
+            int64_t mid = lo + width < n ? lo + width : n;
+            int64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi)
+                tmp[k++] = compare_strings(bytes, offsets, order[j], order[i]) < 0 ? order[j++]
+                                                                                   : order[i++];
+            while (i < mid) tmp[k++] = order[i++];
+            while (j < hi) tmp[k++] = order[j++];
+        }
+        memcpy(order, tmp, (size_t)n * sizeof(uint32_t));
+    }
+    free(tmp);
+    return 0;
 }

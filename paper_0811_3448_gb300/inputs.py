@@ -152,6 +152,36 @@ def config4_segment_sizes(total: int = 256 << 20, count: int = 20000, max_log2: 
     return np.maximum(scaled, 1)
 
 
+def wide_keys(n: int, key_bytes: int, shared_prefix: int = 0, variant: int = 0) -> np.ndarray:
+    """Fixed-width byte-string keys longer than 16 bytes, uint8 of shape
+    (n, key_bytes), uniform bytes; optionally the first `shared_prefix` bytes
+    are one random prefix shared by every key."""
+    g = rng(6, variant)
+    k = g.integers(0, 256, size=(n, key_bytes), dtype=np.uint8)
+    if shared_prefix:
+        k[:, :shared_prefix] = g.integers(0, 256, size=shared_prefix, dtype=np.uint8)
+    return k
+
+
+def strings(n: int, max_len: int = 64, min_len: int = 0, alphabet: int = 256,
+            shared_prefix: int = 0, variant: int = 0):
+    """Variable-length byte strings: lengths uniform in [min_len, max_len],
+    bytes uniform over the first `alphabet` byte values; optionally every
+    string starts with (the first bytes of) one random prefix of
+    `shared_prefix` bytes.  Returns (bytes uint8, offsets int64 of n + 1)."""
+    g = rng(7, variant)
+    lens = g.integers(min_len, max_len + 1, size=n).astype(np.int64)
+    off = offsets_from_sizes(lens)
+    data = g.integers(0, alphabet, size=int(off[-1]), dtype=np.uint8)
+    if shared_prefix:
+        pre = g.integers(0, alphabet, size=shared_prefix, dtype=np.uint8)
+        take = np.minimum(lens, shared_prefix)
+        idx = np.repeat(off[:-1], take) + (np.arange(int(take.sum())) -
+                                          np.repeat(np.cumsum(take) - take, take))
+        data[idx] = pre[idx - np.repeat(off[:-1], take)]
+    return data, off
+
+
 def offsets_from_sizes(sizes: np.ndarray) -> np.ndarray:
     off = np.zeros(len(sizes) + 1, dtype=np.int64)
     np.cumsum(sizes, out=off[1:])

@@ -32,6 +32,11 @@ MUTANTS = {
     "parallel_group_bits": ("g = 2 * g + key_bit(keys + i * kb, kb, map, p);", "g = 2 * g;"),
     "parallel_start_bit": ("jobs[g].pos = b;", "jobs[g].pos = b + 1;"),
     "parallel_group_bounds": ("jobs[g].upper = count[g + 1] - 1;", "jobs[g].upper = count[g + 1] - 2;"),
+    "string_prefix_rule": ("if (la != lb) return la < lb ? -1 : 1;", "if (la != lb) return 0;"),
+    "string_byte_order": ("if (sa[i] != sb[i]) return sa[i] < sb[i] ? -1 : 1;",
+                          "if (sa[i] != sb[i]) return sa[i] > sb[i] ? -1 : 1;"),
+    "string_stability": ("compare_strings(bytes, offsets, order[j], order[i]) < 0",
+                         "compare_strings(bytes, offsets, order[j], order[i]) <= 0"),
 }
 
 
@@ -78,6 +83,11 @@ def _pins_pass(lib) -> bool:
         k2, v2 = k.copy(), v.copy()
         oracle.binar_sort_parallel(k2, v2, log2_groups=4)
         if not (np.array_equal(k2, np.sort(k)) and np.array_equal(k[v2], k2)):
+            return False
+        # strings: prefixes, equal strings in input order
+        data = np.frombuffer(b"ab" + b"a" + b"ab" + b"b" + b"" + b"a", dtype=np.uint8).copy()
+        off = np.array([0, 2, 3, 5, 6, 6, 7], dtype=np.int64)
+        if list(oracle.sort_strings(data, off)) != [4, 1, 5, 0, 2, 3]:
             return False
         return True
     finally:

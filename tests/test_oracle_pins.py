@@ -299,3 +299,77 @@ def test_parallel_variant_agrees_with_binar_sort_on_keys():
             oracle.binar_sort(a)
             oracle.binar_sort_parallel(b, log2_groups=3)
             assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------- long and variable-length keys
+def _string_list(data, off):
+    return [bytes(data[off[i]:off[i + 1]]) for i in range(len(off) - 1)]
+
+
+def test_strings_brute_force_all_short_binary_strings():
+    """Every string over {0, 1} of length 0..5 (63 strings), each twice,
+    shuffled: the order is the sorted list (a proper prefix first) and equal
+    strings keep their input order."""
+    words = [bytes(w) for L in range(6) for w in itertools.product((0, 1), repeat=L)]
+    g = np.random.Generator(np.random.PCG64(31))
+    items = words + words
+    perm = g.permutation(len(items))
+    items = [items[i] for i in perm]
+    off = np.concatenate([[0], np.cumsum([len(w) for w in items])]).astype(np.int64)
+    data = np.frombuffer(b"".join(items), dtype=np.uint8).copy()
+    order = oracle.sort_strings(data, off)
+    assert [items[i] for i in order] == sorted(items)
+    for a, b in zip(order[:-1], order[1:]):           # stable: equal strings in input order
+        if items[a] == items[b]:
+            assert a < b
+
+
+@pytest.mark.parametrize("alphabet,max_len,prefix", [(256, 40, 0), (3, 12, 0), (2, 70, 30),
+                                                     (256, 0, 0)])
+def test_strings_match_python_sorted(alphabet, max_len, prefix):
+    """Python orders bytes lexicographically with a proper prefix first, and
+    sorted() is stable: the library-routine reference."""
+    data, off = inputs.strings(4000, max_len=max_len, alphabet=alphabet, shared_prefix=prefix)
+    items = _string_list(data, off)
+    order = oracle.sort_strings(data, off)
+    assert list(order) == sorted(range(len(items)), key=lambda i: items[i])
+
+
+def test_strings_edge_cases():
+    assert len(oracle.sort_strings(np.zeros(0, np.uint8), np.zeros(1, np.int64))) == 0
+    data = np.frombuffer(b"bab" + b"ba" + b"" + b"b" + b"\x00", dtype=np.uint8).copy()
+    off = np.array([0, 3, 5, 5, 6, 7], dtype=np.int64)   # "bab", "ba", "", "b", "\0"
+    assert list(oracle.sort_strings(data, off)) == [2, 4, 3, 1, 0]
+
+
+@pytest.mark.parametrize("kb", [17, 32, 64, 100, 256])
+def test_wide_byte_string_keys(kb):
+    """Fixed-width keys past 16 bytes: binar sort (bit by bit over all 8*kb
+    bits) gives sorted(bytes); the stable radix sort keeps equal keys in input
+    order; both agree with the string order of the same bytes."""
+    n = 600 if kb == 256 else 2000
+    k = inputs.wide_keys(n, kb, shared_prefix=kb // 2)
+    k[::4] = k[1]
+    keys = k.copy()
+    visits = oracle.binar_sort(keys, key_map=MAP_BYTES_BE)
+    assert [bytes(r) for r in keys] == sorted(bytes(r) for r in k)
+    assert visits <= 8 * kb * n
+    ks, vs = k.copy(), inputs.index_payload(n)
+    oracle.stable_radix(ks, vs, key_map=MAP_BYTES_BE)
+    order = oracle.sort_strings(k.reshape(-1), np.arange(n + 1, dtype=np.int64) * kb)
+    assert np.array_equal(vs, order)
+    assert np.array_equal(ks, k[order])
+
+
+@pytest.mark.parametrize("kb", [32, 48])
+def test_wide_integer_keys(kb):
+    """Little-endian unsigned and two's complement integers of 256 / 384 bits."""
+    g = np.random.Generator(np.random.PCG64(kb))
+    k = g.integers(0, 256, size=(1500, kb), dtype=np.uint8)
+    k[::3, kb // 2:] = 0
+    k[1::5, kb // 2:] = 0xFF
+    for key_map, signed in ((MAP_UNSIGNED, False), (MAP_SIGNED, True)):
+        keys = k.copy()
+        oracle.binar_sort(keys, key_map=key_map)
+        got = [int.from_bytes(bytes(r), "little", signed=signed) for r in keys]
+        assert got == sorted(int.from_bytes(bytes(r), "little", signed=signed) for r in k)
