@@ -32,7 +32,8 @@
  *    full work queue) are written to a status word inside the workspace and
  *    read with binar_workspace_status(); after such an error the output is
  *    unspecified but no write has left the caller's buffers.
- *  - Limits: key_bytes in {4, 8, 16}; val_bytes in {0, 4, 8}; at most
+ *  - Limits: key_bytes in {4, 8, 16} for every call, and 17 .. 256 for
+ *    binar_sort_keys / binar_sort_pairs; val_bytes in {0, 4, 8}; at most
  *    BINAR_MAX_BUCKET_KEYS keys per array or per segment.
  */
 #ifndef BINAR_H
@@ -46,6 +47,7 @@ extern "C" {
 #endif
 
 #define BINAR_MAX_BUCKET_KEYS 2147483646LL
+#define BINAR_MAX_STRING_BYTES 4096LL
 
 /* Key-to-bits maps ("The Other Universal Property": data is sorted by its
  * encoding -- two's complement integers, IEEE-754 floats, byte strings).
@@ -96,6 +98,12 @@ int binar_workspace_bytes(int64_t n, int64_t num_segments, int key_bytes, int va
  * "Algorithm Synopsis" run k bits per pass).
  *   d_keys  device pointer to n keys of key_bytes each (read and written)
  *   map     key-to-bits map; must be valid for key_bytes
+ *   Keys of 17 .. 256 bytes ("The Other Universal Property": byte strings of
+ *   any width; "Recursion Analysis": cost by their length) take BYTES_BE,
+ *   UNSIGNED or SIGNED (little-endian integers of that width) and any byte
+ *   alignment; they are ordered through the windows of binar_sort_strings
+ *   (stable, so the pair form keeps equal keys in input order) and then moved
+ *   into that order.
  *   d_ws    device workspace of ws_bytes >= binar_workspace_bytes(n, 1, key_bytes, 0)
  *   cfg     tuning, or NULL
  *   stream  cudaStream_t
@@ -112,6 +120,31 @@ int binar_sort_pairs(void *d_keys, void *d_vals, int64_t n, int key_bytes, binar
                      int val_bytes, void *d_ws, size_t ws_bytes, const binar_config *cfg,
                      void *stream);
 
+/* Bytes of workspace binar_sort_strings needs for n strings. */
+int binar_strings_workspace_bytes(int64_t n, size_t *out);
+
+/* The stable lexicographic order of n byte strings of different lengths
+ * ("The Other Universal Property": strings are sorted by their encoding; the
+ * paper's cost per string is its length, "Recursion Analysis").  String i is
+ * the bytes d_bytes[d_offsets[i] .. d_offsets[i+1]); bytes compare unsigned,
+ * the first difference decides, a proper prefix comes first, equal strings
+ * keep their input order.
+ *   d_bytes    device pointer to the string bytes (read only)
+ *   d_offsets  device pointer to n + 1 int64, nondecreasing (8-byte aligned)
+ *   max_len    an upper bound on every string's length, <= BINAR_MAX_STRING_BYTES;
+ *              the work runs max_len / 15 + 1 window levels, each of which
+ *              only touches the strings still tied with another one
+ *   d_order    device pointer to n uint32 (4-byte aligned) receiving the order:
+ *              d_order[k] = index of the k-th string
+ *   d_ws       device workspace of ws_bytes >= binar_strings_workspace_bytes(n)
+ * The strings are not moved.  A string longer than max_len is reported as
+ * BINAR_ERR_INVALID_ARG through binar_workspace_status (the order is then
+ * unspecified).  Returns binar_status; like the sort calls it only enqueues
+ * work on `stream`. */
+int binar_sort_strings(const void *d_bytes, const int64_t *d_offsets, int64_t n, int64_t max_len,
+                       uint32_t *d_order, void *d_ws, size_t ws_bytes, const binar_config *cfg,
+                       void *stream);
+
 /* Sorts num_segments independent segments in one call: segment s is
  * [offsets[s], offsets[s+1]) of the key (and payload) arrays.  The segments
  * become the first-level buckets of the recursion ("Algorithm Variants": each
@@ -122,7 +155,8 @@ int binar_sort_pairs(void *d_keys, void *d_vals, int64_t n, int key_bytes, binar
  *              Offsets are read on the device; a decreasing pair is reported as
  *              BINAR_ERR_INVALID_ARG through the status word and that segment is skipped.
  *   ws_bytes   >= binar_workspace_bytes(n, num_segments, key_bytes, val_bytes)
- * Keys outside every segment are not touched. */
+ * Keys outside every segment are not touched.  Keys wider than 16 bytes are
+ * not accepted here (BINAR_ERR_UNSUPPORTED). */
 int binar_sort_segmented(void *d_keys, void *d_vals, const int64_t *d_offsets,
                          int64_t num_segments, int64_t n, int key_bytes, binar_key_map map,
                          int val_bytes, void *d_ws, size_t ws_bytes, const binar_config *cfg,

@@ -14,7 +14,11 @@ uint32 / uint64    4 / 8       UNSIGNED
 int32 / int64      4 / 8       SIGNED
 float32 / float64  4 / 8       FLOAT
 uint8 of (n, 16)   16          BYTES_BE
+uint8 of (n, kb)   17 .. 256   BYTES_BE (sort_keys / sort_pairs only)
 =================  ==========  ==============
+
+Byte strings of different lengths: :func:`sort_strings` (bytes + offsets,
+returns the order).
 
 Payloads: any 4- or 8-byte dtype (moved as opaque bits).
 """
@@ -32,6 +36,8 @@ MAP_UNSIGNED, MAP_SIGNED, MAP_FLOAT, MAP_BYTES_BE = 0, 1, 2, 3
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE_TOO_SMALL = 0, 1, 2, 3
 ERR_CUDA, ERR_DEVICE_TIMEOUT, ERR_DEVICE_BOUNDS, ERR_QUEUE_OVERFLOW = 4, 5, 6, 7
 MAX_BUCKET_KEYS = 2147483646
+MAX_KEY_BYTES = 256
+MAX_STRING_BYTES = 4096
 
 _lib = None
 _lock = threading.Lock()
@@ -88,9 +94,12 @@ def load():
         lib.binar_profile_stop.argtypes = [ctypes.POINTER(KernelStat), i32, ctypes.POINTER(i32)]
         lib.binar_version.restype = ctypes.c_char_p
         lib.binar_generate.argtypes = [p, i64, i32, ctypes.c_uint64, p]
+        lib.binar_strings_workspace_bytes.argtypes = [i64, ctypes.POINTER(sz)]
+        lib.binar_sort_strings.argtypes = [p, p, i64, i64, p, p, sz, cfgp, p]
         for name in ("binar_workspace_bytes", "binar_sort_keys", "binar_sort_pairs",
                      "binar_sort_segmented", "binar_partition_pass", "binar_workspace_status",
-                     "binar_profile_start", "binar_profile_stop", "binar_generate"):
+                     "binar_profile_start", "binar_profile_stop", "binar_generate",
+                     "binar_strings_workspace_bytes", "binar_sort_strings"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -116,8 +125,8 @@ _DEFAULT_MAP = {torch.uint32: MAP_UNSIGNED, torch.uint64: MAP_UNSIGNED,
 
 def key_layout(keys: torch.Tensor):
     """(n, key_bytes, default map) of a key tensor."""
-    if keys.dim() == 2 and keys.dtype == torch.uint8 and keys.shape[1] == 16:
-        return keys.shape[0], 16, MAP_BYTES_BE
+    if keys.dim() == 2 and keys.dtype == torch.uint8 and 16 <= keys.shape[1] <= MAX_KEY_BYTES:
+        return keys.shape[0], keys.shape[1], MAP_BYTES_BE
     if keys.dim() != 1 or keys.dtype not in _DEFAULT_MAP:
         raise TypeError(f"unsupported key tensor {keys.dtype} {tuple(keys.shape)}")
     return keys.shape[0], keys.element_size(), _DEFAULT_MAP[keys.dtype]
@@ -246,6 +255,39 @@ def partition_pass(keys: torch.Tensor, vals: torch.Tensor = None, pos: int = 0, 
                                        _stream(stream)),
            "binar_partition_pass")
     return ko, vo, offs
+
+
+def strings_workspace_bytes(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().binar_strings_workspace_bytes(n, ctypes.byref(out)),
+           "binar_strings_workspace_bytes")
+    return out.value
+
+
+def sort_strings(data: torch.Tensor, offsets: torch.Tensor, max_len: int = None, ws=None,
+                 config=None, stream=None, order=None) -> torch.Tensor:
+    """Stable lexicographic order of the byte strings data[offsets[i]:offsets[i+1]]
+    (binar_sort_strings): returns int32 indices (read as uint32) of the strings
+    in order.  ``max_len`` bounds every string's length (default: computed
+    from ``offsets``, which synchronises)."""
+    _check_dev(data, offsets)
+    if data.dtype != torch.uint8 or data.dim() != 1:
+        raise TypeError("data must be a 1-D uint8 CUDA tensor")
+    if offsets.dtype != torch.int64 or offsets.dim() != 1 or offsets.shape[0] < 1:
+        raise TypeError("offsets must be a 1-D int64 CUDA tensor of n + 1 entries")
+    n = offsets.shape[0] - 1
+    if max_len is None:
+        max_len = int((offsets[1:] - offsets[:-1]).max().item()) if n > 0 else 0
+    if order is None:
+        order = torch.empty(n, dtype=torch.int32, device=data.device)
+    if ws is None:
+        ws = torch.empty(max(strings_workspace_bytes(n), 16), dtype=torch.uint8,
+                         device=data.device)
+    _check_dev(ws, order)
+    _check(load().binar_sort_strings(_ptr(data), _ptr(offsets), n, max_len, _ptr(order),
+                                     _ptr(ws), ws.numel(), _cfg(config), _stream(stream)),
+           "binar_sort_strings")
+    return order
 
 
 def workspace_status(ws: torch.Tensor, stream=None) -> int:

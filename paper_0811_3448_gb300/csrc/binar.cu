@@ -11,6 +11,12 @@ namespace binar {
 int run_call_k4(const Call &c);
 int run_call_k8(const Call &c);
 int run_call_k16(const Call &c);
+int sort_wide(void *keys, void *vals, long long n, int kb, int map, int vb, void *ws,
+              const Call &tuning, cudaStream_t st);
+size_t wide_workspace_bytes(long long n, int kb, int vb);
+size_t strings_workspace_bytes(long long n);
+int sort_strings(const void *bytes, const long long *offsets, long long n, long long max_len,
+                 uint32_t *order, void *ws, const Call &tuning, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Device properties and occupancy, cached per device.
@@ -98,11 +104,20 @@ bool aligned_to(const void *p, int bytes) {
     return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(bytes - 1)) == 0;
 }
 
-int check_types(int key_bytes, int map, int val_bytes) {
-    if (key_bytes != 4 && key_bytes != 8 && key_bytes != 16) return BINAR_ERR_INVALID_ARG;
+constexpr int kMaxWideKeyBytes = 256;
+
+bool wide(int key_bytes) { return key_bytes > 16; }
+
+// allow_wide: the call accepts keys of 17 .. kMaxWideKeyBytes bytes (the
+// unsegmented sorts); the others take 4, 8 or 16.
+int check_types(int key_bytes, int map, int val_bytes, bool allow_wide = false) {
+    if (key_bytes != 4 && key_bytes != 8 && key_bytes != 16) {
+        if (!wide(key_bytes) || key_bytes > kMaxWideKeyBytes) return BINAR_ERR_INVALID_ARG;
+        if (!allow_wide) return BINAR_ERR_UNSUPPORTED;
+    }
     if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return BINAR_ERR_INVALID_ARG;
     if (map < BINAR_MAP_UNSIGNED || map > BINAR_MAP_BYTES_BE) return BINAR_ERR_INVALID_ARG;
-    if (map == BINAR_MAP_FLOAT && key_bytes == 16) return BINAR_ERR_UNSUPPORTED;
+    if (map == BINAR_MAP_FLOAT && key_bytes >= 16) return BINAR_ERR_UNSUPPORTED;
     return BINAR_OK;
 }
 
@@ -161,8 +176,14 @@ extern "C" {
 int binar_workspace_bytes(int64_t n, int64_t num_segments, int key_bytes, int val_bytes,
                           size_t *out) {
     if (!out || n < 0 || num_segments < 0) return BINAR_ERR_INVALID_ARG;
-    if (key_bytes != 4 && key_bytes != 8 && key_bytes != 16) return BINAR_ERR_INVALID_ARG;
+    if (key_bytes != 4 && key_bytes != 8 && key_bytes != 16 &&
+        !(wide(key_bytes) && key_bytes <= kMaxWideKeyBytes))
+        return BINAR_ERR_INVALID_ARG;
     if (val_bytes != 0 && val_bytes != 4 && val_bytes != 8) return BINAR_ERR_INVALID_ARG;
+    if (wide(key_bytes)) {
+        *out = wide_workspace_bytes(n, key_bytes, val_bytes);
+        return BINAR_OK;
+    }
     *out = make_layout(n, num_segments > 0 ? num_segments : 1, key_bytes, val_bytes).total;
     return BINAR_OK;
 }
@@ -170,16 +191,31 @@ int binar_workspace_bytes(int64_t n, int64_t num_segments, int key_bytes, int va
 static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int64_t num_segments,
                        int64_t n, int key_bytes, binar_key_map map, int val_bytes, void *d_ws,
                        size_t ws_bytes, const binar_config *cfg, void *stream) {
-    int rc = check_types(key_bytes, map, val_bytes);
+    int rc = check_types(key_bytes, map, val_bytes, d_offsets == nullptr);
     if (rc) return rc;
     if (n < 0) return BINAR_ERR_INVALID_ARG;
     if (!d_offsets && n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_UNSUPPORTED;
     if (d_offsets && num_segments < 0) return BINAR_ERR_INVALID_ARG;
-    if (n > 0 && (!d_keys || !aligned_to(d_keys, key_bytes))) return BINAR_ERR_INVALID_ARG;
+    if (n > 0 && (!d_keys || (!wide(key_bytes) && !aligned_to(d_keys, key_bytes))))
+        return BINAR_ERR_INVALID_ARG;
     if (val_bytes && n > 0 && (!d_vals || !aligned_to(d_vals, val_bytes))) return BINAR_ERR_INVALID_ARG;
     if (!val_bytes && d_vals) return BINAR_ERR_INVALID_ARG;
     if (!d_ws || !aligned16(d_ws)) return BINAR_ERR_INVALID_ARG;
     const long long segs = d_offsets ? (num_segments > 0 ? num_segments : 1) : 1;
+    if (wide(key_bytes)) {
+        // keys past 16 bytes: window levels over the 16-byte sort (whose tile,
+        // bits and cutoff the config sets)
+        if (ws_bytes < wide_workspace_bytes(n, key_bytes, val_bytes))
+            return BINAR_ERR_WORKSPACE_TOO_SMALL;
+        Call t = blank_call();
+        if ((rc = resolve_config(cfg, 16, 4, t))) return rc;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (n == 0)
+            return cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) == cudaSuccess ? BINAR_OK
+                                                                             : BINAR_ERR_CUDA;
+        return sort_wide(d_keys, val_bytes ? d_vals : nullptr, n, key_bytes, map, val_bytes, d_ws,
+                         t, s);
+    }
     if (ws_bytes < make_layout(n, segs, key_bytes, val_bytes).total)
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
@@ -270,6 +306,33 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
     c.ws = d_ws;
     c.stream = s;
     return dispatch(c, key_bytes);
+}
+
+int binar_strings_workspace_bytes(int64_t n, size_t *out) {
+    if (!out || n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
+    *out = strings_workspace_bytes(n);
+    return BINAR_OK;
+}
+
+int binar_sort_strings(const void *d_bytes, const int64_t *d_offsets, int64_t n, int64_t max_len,
+                       uint32_t *d_order, void *d_ws, size_t ws_bytes, const binar_config *cfg,
+                       void *stream) {
+    if (n < 0 || n > BINAR_MAX_BUCKET_KEYS || max_len < 0 || max_len > BINAR_MAX_STRING_BYTES)
+        return BINAR_ERR_INVALID_ARG;
+    if (n > 0 && (!d_offsets || !d_order || (!d_bytes && max_len > 0)))
+        return BINAR_ERR_INVALID_ARG;
+    if (!d_ws || !aligned16(d_ws)) return BINAR_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_offsets) & 7) || (reinterpret_cast<uintptr_t>(d_order) & 3))
+        return BINAR_ERR_INVALID_ARG;
+    if (ws_bytes < strings_workspace_bytes(n)) return BINAR_ERR_WORKSPACE_TOO_SMALL;
+    Call t = blank_call();
+    int rc = resolve_config(cfg, 16, 4, t);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0)
+        return cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) == cudaSuccess ? BINAR_OK : BINAR_ERR_CUDA;
+    return sort_strings(d_bytes, reinterpret_cast<const long long *>(d_offsets), n, max_len, d_order,
+                        d_ws, t, s);
 }
 
 int binar_workspace_status(void *d_ws, void *stream, int *out_status) {

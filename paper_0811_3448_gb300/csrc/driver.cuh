@@ -12,15 +12,22 @@
 
 namespace binar {
 
+// Grids are persistent (occupancy x SMs) but never larger than the work a
+// call of n keys can hold, so that small sorts do not launch idle CTAs.
+inline int cap_grid(long long grid, long long work) {
+    if (work < 1) work = 1;
+    return (int)(grid < work ? grid : work);
+}
+
 template <int KB, int VB, bool STABLE, int TV>
 int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int level,
-                     void *k0, void *k1, void *v0, void *v1) {
+                     void *k0, void *k1, void *v0, void *v1, long long max_tiles) {
     auto kfn = p.map == BINAR_MAP_UNSIGNED ? k_partition<KB, VB, STABLE, true, TV>
                                            : k_partition<KB, VB, STABLE, false, TV>;
     const size_t smem = sizeof(PartitionSmem<KB, VB, STABLE, TV>);
     int occ = kernel_ctas_per_sm((const void *)kfn, smem);
     if (c.ctas_per_sm > 0 && c.ctas_per_sm < occ) occ = c.ctas_per_sm;
-    const int grid = device_sms() * (occ > 0 ? occ : 1);
+    const int grid = cap_grid((long long)device_sms() * (occ > 0 ? occ : 1), max_tiles);
     return launch("partition", level, c.stream, [&] {
         launch_pdl(kfn, grid, kThreads, smem, c.stream, ws, p, slot, level, k0, k1, v0, v1);
     });
@@ -39,8 +46,11 @@ int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, 
                                                          : k_finish<KB, VB, CLS, false>;
     const size_t smem = sizeof(FinishSmem<KB, VB, IU>);
     const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
+    // jobs of this class hold more keys than the class below it can
+    const long long lower = CLS > 0 ? (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) : 1;
+    const int grid = cap_grid((long long)device_sms() * (occ > 0 ? occ : 1), c.n / (lower + 1) + 1);
     return launch("finish", CLS, c.stream, [&] {
-        launch_pdl(ffn, device_sms() * (occ > 0 ? occ : 1), kThreads, smem, c.stream, ws, p, k0, k1, v0, v1);
+        launch_pdl(ffn, grid, kThreads, smem, c.stream, ws, p, k0, k1, v0, v1);
     });
 }
 
@@ -87,8 +97,9 @@ int run_call_vb(const Call &c) {
         {
             auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
             const int occ = kernel_ctas_per_sm((const void *)hfn, 0);
+            const int hg = cap_grid((long long)sms * (occ > 0 ? occ : 1), tiles / kHistGroup + 1);
             if ((rc = launch("hist", 0, c.stream, [&] {
-                     launch_pdl(hfn, sms * (occ > 0 ? occ : 1), kThreads, 0, c.stream, ws, p, 0, 0);
+                     launch_pdl(hfn, hg, kThreads, 0, c.stream, ws, p, 0, 0);
                  })))
                 return rc;
         }
@@ -97,7 +108,8 @@ int run_call_vb(const Call &c) {
              })))
             return rc;
         return launch_partition<KB, VB, true, 0>(c, ws, p, 0, 1, const_cast<void *>(c.keys_in),
-                                                 c.keys_out, const_cast<void *>(c.vals_in), c.vals_out);
+                                                 c.keys_out, const_cast<void *>(c.vals_in), c.vals_out,
+                                                 tiles);
     }
 
     p.keys = c.keys;
@@ -105,6 +117,10 @@ int run_call_vb(const Call &c) {
     void *k0 = c.keys, *k1 = ws.alt_keys, *v0 = c.vals, *v1 = VB ? ws.alt_vals : nullptr;
     const bool seg = c.offsets != nullptr;
     const uint32_t tiles0 = (uint32_t)((c.n + T - 1) / T);
+    // work bounds: every bucket of a level holds more than `cutoff` keys, and
+    // has at most one partial tile
+    const long long max_buckets = c.n / ((long long)c.cutoff + 1) + 1;
+    const long long max_tiles = c.n / T + max_buckets + 1;
     if ((rc = launch("init", -1, c.stream, [&] {
              launch_pdl(k_init<KB>, 1, 1, 0, c.stream, ws, c.n, c.cutoff, 0, tiles0, seg ? 0 : 1);
          })))
@@ -115,18 +131,21 @@ int run_call_vb(const Call &c) {
         if (grid > small_grid) grid = small_grid;
         if (grid < 1) grid = 1;
         if ((rc = launch("seed", -1, c.stream, [&] {
-                 launch_pdl(k_seed_segments<KB>, grid, kThreads, 0, c.stream, ws, c.offsets, S, c.n, c.cutoff, T);
+                 launch_pdl(k_seed_segments<KB>, grid, kThreads, 0, c.stream, ws, c.offsets, S, c.n, c.cutoff, T,
+                            c.num_segments_dev);
              })))
             return rc;
     }
     if (seg || c.n > c.cutoff) {
         auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
         const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
-        const int hgrid = sms * (hocc > 0 ? hocc : 1);
+        const int hgrid = cap_grid((long long)sms * (hocc > 0 ? hocc : 1), max_tiles / kHistGroup + 1);
+        const int pgrid = cap_grid(small_grid, max_buckets > max_tiles / 4 ? max_buckets : max_tiles / 4);
+        const int cgrid = cap_grid(small_grid, max_buckets);
         for (int l = 0; l < L; l++) {
             const int slot = l & 1;
             if ((rc = launch("prep", l, c.stream, [&] {
-                     launch_pdl(k_prep, small_grid, kThreads, 0, c.stream, ws, slot);
+                     launch_pdl(k_prep, pgrid, kThreads, 0, c.stream, ws, slot);
                  })))
                 return rc;
             if ((rc = launch("hist", l, c.stream, [&] {
@@ -134,17 +153,18 @@ int run_call_vb(const Call &c) {
                  })))
                 return rc;
             if ((rc = launch("classify", l, c.stream, [&] {
-                     launch_pdl(k_classify<KB>, small_grid, kThreads, 0, c.stream, ws, p, slot, l == L - 1);
+                     launch_pdl(k_classify<KB>, cgrid, kThreads, 0, c.stream, ws, p, slot, l == L - 1);
                  })))
                 return rc;
-            if ((rc = tv ? launch_partition<KB, VB, STABLE, 1>(c, ws, p, slot, l, k0, k1, v0, v1)
-                         : launch_partition<KB, VB, STABLE, 0>(c, ws, p, slot, l, k0, k1, v0, v1)))
+            if ((rc = tv ? launch_partition<KB, VB, STABLE, 1>(c, ws, p, slot, l, k0, k1, v0, v1, max_tiles)
+                         : launch_partition<KB, VB, STABLE, 0>(c, ws, p, slot, l, k0, k1, v0, v1, max_tiles)))
                 return rc;
         }
     }
     {
         if ((rc = launch("bin_jobs", -1, c.stream, [&] {
-                 launch_pdl(k_bin_jobs<KB>, small_grid, kThreads, 0, c.stream, ws);
+                 launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
+                            c.stream, ws);
              })))
             return rc;
         if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k1, v0, v1,
@@ -154,12 +174,14 @@ int run_call_vb(const Call &c) {
         const size_t lsmem = sizeof(FinishLsdSmem<KB, VB>);
         const int locc = kernel_ctas_per_sm((const void *)lfn, lsmem);
         if ((rc = launch("finish_lsd", -1, c.stream, [&] {
-                 launch_pdl(lfn, sms * (locc > 0 ? locc : 1), kThreads, lsmem, c.stream, ws, p, k0, k1, v0, v1);
+                 launch_pdl(lfn, cap_grid((long long)sms * (locc > 0 ? locc : 1), c.n / 33 + 1), kThreads,
+                            lsmem, c.stream, ws, p, k0, k1, v0, v1);
              })))
             return rc;
     }
     return launch("copy", -1, c.stream, [&] {
-        launch_pdl(k_copy<KB, VB>, small_grid, kThreads, 0, c.stream, ws, T, k0, k1, v0, v1);
+        launch_pdl(k_copy<KB, VB>, cap_grid(small_grid, max_tiles), kThreads, 0, c.stream, ws, T, k0, k1,
+                   v0, v1);
     });
 }
 

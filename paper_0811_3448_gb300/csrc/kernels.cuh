@@ -425,10 +425,17 @@ __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0
 // seed_segments: segment s = [offsets[s], offsets[s+1]) becomes a level-0
 // bucket (more than `cutoff` keys), a finisher job (2..cutoff keys) or
 // nothing (0 or 1 key).
+// count_dev: if not null, the number of segments is read from device memory
+// (at most num_segments), for callers whose segment count is known only on
+// the device.
 template <int KB>
 __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_segments,
-                                long long n, int cutoff, int tile) {
+                                long long n, int cutoff, int tile, const long long *count_dev) {
     pdl_entry();
+    if (count_dev) {
+        const long long c = *count_dev;
+        num_segments = c < num_segments ? (c > 0 ? c : 0) : num_segments;
+    }
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < num_segments;
          s += stride) {

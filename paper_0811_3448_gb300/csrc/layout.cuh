@@ -171,7 +171,8 @@ struct Call {
     bool pass_mode;
     const Layout *layout;          // workspace layout to use instead of make_layout(), or nullptr
     const long long *offsets;      // segmented: device offsets, else nullptr
-    long long num_segments;
+    long long num_segments;        // segmented: segments (an upper bound if num_segments_dev is set)
+    const long long *num_segments_dev;   // segmented: device-side segment count, or nullptr
     long long n;
     int map, vb;
     int cutoff;

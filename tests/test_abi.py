@@ -117,3 +117,32 @@ def test_argument_checks_need_no_gpu(lib):
                                     aligned, big, None, None) == binding.ERR_UNSUPPORTED
     assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 4, 0, 0, 0, -1, None,
                                     aligned, big, None, None) == binding.ERR_UNSUPPORTED
+
+
+def test_wide_keys_and_strings_argument_checks(lib):
+    aligned = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    # keys of 17 .. 256 bytes: the unsegmented sorts only, no FLOAT map
+    assert _call_keys(lib, aligned, 10, 257, 3, aligned, big) == binding.ERR_INVALID_ARG
+    assert _call_keys(lib, aligned, 10, 32, binding.MAP_FLOAT, aligned, big) == \
+        binding.ERR_UNSUPPORTED
+    assert lib.binar_sort_segmented(aligned, None, aligned, 1, 10, 32, 3, 0, aligned, big, None,
+                                    None) == binding.ERR_UNSUPPORTED
+    assert lib.binar_partition_pass(aligned, None, aligned, None, 10, 32, 3, 0, 0, 8, None,
+                                    aligned, big, None, None) == binding.ERR_UNSUPPORTED
+    assert _call_keys(lib, aligned, 1000, 64, 3, aligned, 16) == binding.ERR_WORKSPACE_TOO_SMALL
+    assert binding.workspace_bytes(1000, 64, 8) > 1000 * 64
+    with pytest.raises(binding.BinarError):
+        binding.workspace_bytes(10, 300, 0)
+    # strings: length bound, pointer alignment, workspace size
+    sws = binding.strings_workspace_bytes(1000)
+    assert sws > binding.strings_workspace_bytes(10) > 0
+    f = lib.binar_sort_strings
+    assert f(aligned, aligned, 10, binding.MAX_STRING_BYTES + 1, aligned, aligned, big, None,
+             None) == binding.ERR_INVALID_ARG
+    assert f(aligned, ctypes.c_void_p(0x1004), 10, 8, aligned, aligned, big, None, None) == \
+        binding.ERR_INVALID_ARG
+    assert f(aligned, aligned, 10, 8, ctypes.c_void_p(0x1002), aligned, big, None, None) == \
+        binding.ERR_INVALID_ARG
+    assert f(aligned, aligned, 1000, 8, aligned, aligned, 16, None, None) == \
+        binding.ERR_WORKSPACE_TOO_SMALL
