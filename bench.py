@@ -55,10 +55,11 @@ def parse_args():
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--workload", choices=["pairs", "segments", "serve"], default="pairs",
+    ap.add_argument("--workload", choices=["pairs", "segments", "serve", "inplace"], default="pairs",
                     help="pairs: 256M uint32+uint32 sort (the headline); segments: 20,000 "
                          "segments in one CUDA-graph launch vs one call per segment; serve: "
-                         "the continuous-batching request loop vs one request per launch")
+                         "the continuous-batching request loop vs one request per launch; "
+                         "inplace: the same pairs sorted by the unstable in-place mode")
     ap.add_argument("--seg-len", type=int, default=0,
                     help="segments: equal segments of this many keys instead of the "
                          "20,000 log-uniform ones")
@@ -99,14 +100,17 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# the files that hold the partition and finisher kernels and their helpers
+KERNEL_FILES = ("binar_internal.cuh", "kernels.cuh")
+
+
 def kernel_source_hash():
-    """Hash of the kernel sources' code: comments and whitespace are dropped,
-    so that a comment edit does not mark recorded counters as stale."""
+    """Hash of the code of the files that hold the timed kernels: comments and
+    whitespace are dropped, so that a comment edit does not mark recorded
+    counters as stale, and code elsewhere in the library does not count."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0811_3448_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if not name.endswith((".cu", ".cuh", ".h")):
-            continue
+    for name in KERNEL_FILES:
         with open(os.path.join(csrc, name)) as f:
             code = f.read()
         code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
@@ -704,12 +708,85 @@ def run_segments(args):
         print(json.dumps(out), flush=True)
 
 
+def run_inplace(args):
+    """The pairs workload sorted by binar_sort_inplace (unstable, no second
+    array), timed like the headline; reports the workspace beside the
+    out-of-place sort's."""
+    import torch
+    from paper_0811_3448_gb300 import binding, inputs
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    kb = 8 if args.key == "u64" else 4
+    kdt = np.uint64 if kb == 8 else np.uint32
+    keys0 = torch.from_numpy(inputs.config2_keys(n, kdt, args.dist)).to(dev)
+    vals0 = torch.from_numpy(inputs.index_payload(n)).to(dev)
+    keys, vals = torch.empty_like(keys0), torch.empty_like(vals0)
+    wsb = binding.inplace_workspace_bytes(n, kb, 4)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        binding.sort_inplace(keys, vals, ws=ws)
+    binding.check_status(ws)
+    sampler = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        evs[i][0].record(stream)
+        binding.sort_inplace(keys, vals, ws=ws)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    binding.check_status(ws)
+    binding.profile_start()
+    for i in range(min(args.steps, 3)):
+        keys.copy_(keys0)
+        vals.copy_(vals0)
+        binding.sort_inplace(keys, vals, ws=ws)
+    torch.cuda.synchronize()
+    kst = binding.profile_stop()
+    sampler.stop()
+    binding.check_status(ws)
+    per = {}
+    for name, (launches, t) in kst.items():      # summed over the levels, per sort
+        base = name.split("[")[0]
+        per[base] = per.get(base, 0.0) + t / min(args.steps, 3)
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ref = keys0.clone()
+    binding.sort_keys(ref)
+    vv = vals.to(torch.int64)
+    valid = bool(torch.equal(keys, ref)) and bool((torch.bincount(vv, minlength=n) == 1).all()) \
+        and bool(torch.equal(keys0.to(torch.int64)[vv], keys.to(torch.int64)))
+    out = {"metric": METRIC, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.key,
+           "data": "synthetic",
+           "config": {"workload": workload_name(n, args.key, args.dist).replace(
+                          "stable in-place sort", "unstable in-place mode (one bit per level)"),
+                      "n": n, "parallelism": "replicas x1",
+                      "l2": "inputs > 129 MB L2, restored from a pristine copy before every sort"},
+           "workspace_bytes": wsb, "out_of_place_workspace_bytes": binding.workspace_bytes(n, kb, 4),
+           "kernels_ms_per_sort": {k: round(v, 4) for k, v in sorted(per.items(), key=lambda x: -x[1])},
+           "validated": valid, "clocks": sampler.summary()}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "segments":
         run_segments(args)
+    elif args.workload == "inplace":
+        run_inplace(args)
     elif args.workload == "serve":
         from paper_0811_3448_gb300 import serve
         sampler = ClockSampler(dist_env()[2])

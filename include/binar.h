@@ -80,7 +80,8 @@ typedef struct {
                                keys) */
     int bits_per_pass;      /* k, key bits consumed per partition pass: 0 or 8 */
     int small_cutoff;       /* C: buckets of <= C keys are finished in shared memory;
-                               2048 .. the finisher capacity for the key/payload size */
+                               2048 .. the finisher capacity: 8192 / 4096 / 2048
+                               keys for 4 / 8 / 16-byte keys (0: the capacity) */
     int ctas_per_sm;        /* persistent CTAs per SM for the partition kernels (0 = max) */
     int64_t lookback_timeout_ns; /* limit on one look-back wait (0 = 1 s) */
     int debug_skip_publish_tile; /* TEST HOOK: if > 0, tile (value-1) of the first partition
@@ -119,6 +120,31 @@ int binar_sort_keys(void *d_keys, int64_t n, int key_bytes, binar_key_map map,
 int binar_sort_pairs(void *d_keys, void *d_vals, int64_t n, int key_bytes, binar_key_map map,
                      int val_bytes, void *d_ws, size_t ws_bytes, const binar_config *cfg,
                      void *stream);
+
+/* Bytes of workspace binar_sort_inplace needs for n keys of key_bytes with
+ * val_bytes of payload and the config's cutoff (cfg may be NULL).  About one
+ * bit per key plus a few words per bucket, tile and finisher job: for 256M
+ * uint32 keys and payloads a few hundred MB, against the 2 GiB second array
+ * of the other sorts. */
+int binar_inplace_workspace_bytes(int64_t n, int key_bytes, int val_bytes,
+                                  const binar_config *cfg, size_t *out);
+
+/* Sorts n keys (and payloads) in place and unstably, as the paper's algorithm
+ * does ("Partition Array into Sub-arrays": one bit per pass, misplaced
+ * elements exchanged between the lower and the upper sub-array; "Space
+ * Analysis": no second array; "Conclusion": unstable).  Every live sub-array
+ * of a level is split on its next bit at once: the k-th element with bit 1
+ * below the split point is exchanged with the k-th element with bit 0 above
+ * it; sub-arrays of at most the cutoff are finished in shared memory and
+ * written back in place.  Keys come out in the same order as binar_sort_keys;
+ * records with equal keys come out in an unspecified order.
+ *   Arguments as binar_sort_pairs (d_vals NULL and val_bytes 0 for keys only);
+ *   key_bytes in {4, 8, 16}; cfg may set small_cutoff and the wait limit (tile
+ *   and bits per pass are fixed: 1024-key tiles, one bit);
+ *   ws_bytes >= binar_inplace_workspace_bytes(n, key_bytes, val_bytes, cfg). */
+int binar_sort_inplace(void *d_keys, void *d_vals, int64_t n, int key_bytes, binar_key_map map,
+                       int val_bytes, void *d_ws, size_t ws_bytes, const binar_config *cfg,
+                       void *stream);
 
 /* Bytes of workspace binar_sort_strings needs for n strings. */
 int binar_strings_workspace_bytes(int64_t n, size_t *out);

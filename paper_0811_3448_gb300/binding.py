@@ -95,11 +95,14 @@ def load():
         lib.binar_version.restype = ctypes.c_char_p
         lib.binar_generate.argtypes = [p, i64, i32, ctypes.c_uint64, p]
         lib.binar_strings_workspace_bytes.argtypes = [i64, ctypes.POINTER(sz)]
+        lib.binar_inplace_workspace_bytes.argtypes = [i64, i32, i32, cfgp, ctypes.POINTER(sz)]
+        lib.binar_sort_inplace.argtypes = [p, p, i64, i32, i32, i32, p, sz, cfgp, p]
         lib.binar_sort_strings.argtypes = [p, p, i64, i64, p, p, sz, cfgp, p]
         for name in ("binar_workspace_bytes", "binar_sort_keys", "binar_sort_pairs",
                      "binar_sort_segmented", "binar_partition_pass", "binar_workspace_status",
                      "binar_profile_start", "binar_profile_stop", "binar_generate",
-                     "binar_strings_workspace_bytes", "binar_sort_strings"):
+                     "binar_strings_workspace_bytes", "binar_sort_strings",
+                     "binar_inplace_workspace_bytes", "binar_sort_inplace"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -255,6 +258,34 @@ def partition_pass(keys: torch.Tensor, vals: torch.Tensor = None, pos: int = 0, 
                                        _stream(stream)),
            "binar_partition_pass")
     return ko, vo, offs
+
+
+def inplace_workspace_bytes(n: int, key_bytes: int, val_bytes: int = 0, config=None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().binar_inplace_workspace_bytes(n, key_bytes, val_bytes, _cfg(config),
+                                                ctypes.byref(out)),
+           "binar_inplace_workspace_bytes")
+    return out.value
+
+
+def sort_inplace(keys: torch.Tensor, vals: torch.Tensor = None, key_map=None, ws=None,
+                 config=None, stream=None):
+    """Sorts keys (and payloads) in place and unstably (binar_sort_inplace):
+    the paper's one-bit exchange passes, no second array."""
+    _check_dev(keys, vals)
+    n, kb, dmap = key_layout(keys)
+    vb = _val_bytes(vals)
+    if vals is not None and vals.shape[0] != n:
+        raise ValueError("keys and vals differ in length")
+    if ws is None:
+        ws = torch.empty(max(inplace_workspace_bytes(n, kb, vb, config), 16), dtype=torch.uint8,
+                         device=keys.device)
+    _check_dev(ws)
+    _check(load().binar_sort_inplace(_ptr(keys), _ptr(vals), n, kb,
+                                     dmap if key_map is None else key_map, vb, _ptr(ws),
+                                     ws.numel(), _cfg(config), _stream(stream)),
+           "binar_sort_inplace")
+    return keys, vals
 
 
 def strings_workspace_bytes(n: int) -> int:

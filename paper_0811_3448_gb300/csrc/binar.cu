@@ -125,9 +125,9 @@ int check_types(int key_bytes, int map, int val_bytes, bool allow_wide = false) 
 // min_bits: the smallest bits per pass the call accepts (a sort bounds its
 // level count by kMinSortBits; a single pass takes any width down to 1).
 int resolve_config(const binar_config *cfg, int key_bytes, int val_bytes, Call &c,
-                   int min_bits = kMinSortBits) {
-    const int cap = finish_cap_for(key_bytes);
-    c.cutoff = cap;
+                   int min_bits = kMinSortBits, long long n = 0) {
+    const int cap = finish_cap_for(key_bytes, val_bytes);
+    c.cutoff = default_cutoff(key_bytes, val_bytes, n);
     c.ctas_per_sm = 0;
     c.timeout_ns = 1000000000LL;
     c.skip_publish_tile = -1;
@@ -208,7 +208,7 @@ static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int
         if (ws_bytes < wide_workspace_bytes(n, key_bytes, val_bytes))
             return BINAR_ERR_WORKSPACE_TOO_SMALL;
         Call t = blank_call();
-        if ((rc = resolve_config(cfg, 16, 4, t))) return rc;
+        if ((rc = resolve_config(cfg, 16, 4, t, kMinSortBits, n))) return rc;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         if (n == 0)
             return cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) == cudaSuccess ? BINAR_OK
@@ -219,7 +219,7 @@ static int sort_common(void *d_keys, void *d_vals, const int64_t *d_offsets, int
     if (ws_bytes < make_layout(n, segs, key_bytes, val_bytes).total)
         return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call c = blank_call();
-    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c))) return rc;
+    if ((rc = resolve_config(cfg, key_bytes, val_bytes, c, kMinSortBits, n))) return rc;
     if (n == 0 || (d_offsets && num_segments == 0)) {
         // nothing to sort; the status word still reports this call
         if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), static_cast<cudaStream_t>(stream)) !=
@@ -308,6 +308,65 @@ int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_k
     return dispatch(c, key_bytes);
 }
 
+// Cutoff of an in-place call (the config's, else the finisher's capacity);
+// tile and bits per pass are fixed in that mode.
+static int inplace_cutoff(const binar_config *cfg, int key_bytes, int val_bytes, long long n,
+                          int *cutoff) {
+    *cutoff = default_cutoff(key_bytes, val_bytes, n);
+    if (!cfg) return BINAR_OK;
+    if (cfg->tile_keys != 0 || (cfg->bits_per_pass != 0 && cfg->bits_per_pass != 1))
+        return BINAR_ERR_UNSUPPORTED;
+    if (cfg->small_cutoff != 0) {
+        if (cfg->small_cutoff < kMinCutoff || cfg->small_cutoff > finish_cap_for(key_bytes, val_bytes))
+            return BINAR_ERR_INVALID_ARG;
+        *cutoff = cfg->small_cutoff;
+    }
+    if (cfg->ctas_per_sm < 0 || cfg->lookback_timeout_ns < 0) return BINAR_ERR_INVALID_ARG;
+    return BINAR_OK;
+}
+
+int binar_inplace_workspace_bytes(int64_t n, int key_bytes, int val_bytes, const binar_config *cfg,
+                                  size_t *out) {
+    if (!out || n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
+    int rc = check_types(key_bytes, BINAR_MAP_UNSIGNED, val_bytes);
+    if (rc) return rc;
+    int cutoff = 0;
+    if ((rc = inplace_cutoff(cfg, key_bytes, val_bytes, n, &cutoff))) return rc;
+    *out = make_inplace_layout(n, key_bytes, cutoff).end;
+    return BINAR_OK;
+}
+
+int binar_sort_inplace(void *d_keys, void *d_vals, int64_t n, int key_bytes, binar_key_map map,
+                       int val_bytes, void *d_ws, size_t ws_bytes, const binar_config *cfg,
+                       void *stream) {
+    int rc = check_types(key_bytes, map, val_bytes);
+    if (rc) return rc;
+    if (n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
+    if (n > 0 && (!d_keys || !aligned_to(d_keys, key_bytes))) return BINAR_ERR_INVALID_ARG;
+    if (val_bytes && n > 0 && (!d_vals || !aligned_to(d_vals, val_bytes))) return BINAR_ERR_INVALID_ARG;
+    if (!val_bytes && d_vals) return BINAR_ERR_INVALID_ARG;
+    if (!d_ws || !aligned16(d_ws)) return BINAR_ERR_INVALID_ARG;
+    int cutoff = 0;
+    if ((rc = inplace_cutoff(cfg, key_bytes, val_bytes, n, &cutoff))) return rc;
+    if (ws_bytes < make_inplace_layout(n, key_bytes, cutoff).end) return BINAR_ERR_WORKSPACE_TOO_SMALL;
+    Call c = blank_call();
+    if ((rc = resolve_config(nullptr, key_bytes, val_bytes, c))) return rc;
+    c.cutoff = cutoff;
+    if (cfg && cfg->lookback_timeout_ns > 0) c.timeout_ns = cfg->lookback_timeout_ns;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0)
+        return cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), s) == cudaSuccess ? BINAR_OK : BINAR_ERR_CUDA;
+    c.inplace = true;
+    c.keys = d_keys;
+    c.vals = val_bytes ? d_vals : nullptr;
+    c.n = n;
+    c.map = map;
+    c.vb = val_bytes;
+    c.ws = d_ws;
+    c.stream = s;
+    return dispatch(c, key_bytes);
+}
+
 int binar_strings_workspace_bytes(int64_t n, size_t *out) {
     if (!out || n < 0 || n > BINAR_MAX_BUCKET_KEYS) return BINAR_ERR_INVALID_ARG;
     *out = strings_workspace_bytes(n);
@@ -326,7 +385,7 @@ int binar_sort_strings(const void *d_bytes, const int64_t *d_offsets, int64_t n,
         return BINAR_ERR_INVALID_ARG;
     if (ws_bytes < strings_workspace_bytes(n)) return BINAR_ERR_WORKSPACE_TOO_SMALL;
     Call t = blank_call();
-    int rc = resolve_config(cfg, 16, 4, t);
+    int rc = resolve_config(cfg, 16, 4, t, kMinSortBits, n);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0)

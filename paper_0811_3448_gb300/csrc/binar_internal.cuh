@@ -119,6 +119,7 @@ struct Params {
     int skip_publish_tile;         // test hook: level-0 tile that never publishes (-1 = none)
     int tile;                      // keys per partition tile (the call's tile variant)
     int bits;                      // k: key bits per partition pass, 1 .. kBits
+    int inplace;                   // 1: children stay in the caller's arrays (in-place passes)
 };
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 
 #include <utility>
 
+#include "inplace.cuh"
 #include "kernels.cuh"
 #include "layout.cuh"
 
@@ -62,8 +63,114 @@ int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0
     return rc;
 }
 
+// The in-place, unstable mode: one bit per level, keys exchanged across each
+// bucket's split point inside the caller's arrays (inplace.cuh), buckets of
+// at most `cutoff` keys finished in shared memory and written back in place.
+template <int KB, int VB>
+int run_inplace(const Call &c) {
+    const int sms = device_sms();
+    if (sms <= 0) return BINAR_ERR_CUDA;
+    const InplaceLayout IL = make_inplace_layout(c.n, KB, c.cutoff);
+    Ws ws = carve(IL.base, c.ws);
+    ws.cells = nullptr;            // no look-back cells (and none allocated)
+    ws.alt_keys = nullptr;         // no second array
+    ws.alt_vals = nullptr;
+    unsigned char *wb = static_cast<unsigned char *>(c.ws);
+    IpWs ip;
+    ip.mask = reinterpret_cast<uint32_t *>(wb + IL.mask);
+    ip.cnt = reinterpret_cast<uint32_t *>(wb + IL.cnt);
+    ip.pre = reinterpret_cast<uint32_t *>(wb + IL.pre);
+    ip.bsum = reinterpret_cast<uint32_t *>(wb + IL.bsum);
+    ip.total = reinterpret_cast<unsigned long long *>(wb + IL.total);
+    ip.first = reinterpret_cast<uint32_t *>(wb + IL.first);
+    ip.chunk_cap = IL.chunks;
+    Params p{};
+    p.keys = c.keys;
+    p.vals = c.vals;
+    p.map = c.map;
+    p.n = c.n;
+    p.cutoff = c.cutoff;
+    p.timeout_ns = c.timeout_ns;
+    p.skip_publish_tile = -1;
+    p.tile = kIpTile;
+    p.bits = 1;
+    p.inplace = 1;
+    const int L = levels_for(KB, 1);
+    const int small_grid = sms * 4;
+    const long long max_buckets = c.n / ((long long)c.cutoff + 1) + 1;
+    const long long max_tiles = c.n / kIpTile + max_buckets + 1;
+    void *k0 = c.keys, *v0 = c.vals;
+    int rc;
+    if ((rc = launch("init", -1, c.stream, [&] {
+             launch_pdl(k_init<KB>, 1, 1, 0, c.stream, ws, c.n, c.cutoff, 0,
+                        (uint32_t)((c.n + kIpTile - 1) / kIpTile), 1);
+         })))
+        return rc;
+    if (c.n > c.cutoff) {
+        auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
+        auto cfn = c.map == BINAR_MAP_UNSIGNED ? k_ip_count<KB, true> : k_ip_count<KB, false>;
+        const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
+        const int hgrid = cap_grid((long long)sms * (hocc > 0 ? hocc : 1), max_tiles / kHistGroup + 1);
+        const int pgrid = cap_grid(small_grid, max_buckets > max_tiles / 4 ? max_buckets : max_tiles / 4);
+        const int cgrid = cap_grid(small_grid, max_buckets);
+        const int tgrid = cap_grid((long long)sms * 8, max_tiles);
+        const int sgrid = cap_grid(small_grid, max_tiles / kIpScanTile + 1);
+        const int wgrid = cap_grid(small_grid, c.n / (2LL * kIpChunk) + 1);
+        for (int l = 0; l < L; l++) {
+            const int slot = l & 1;
+            if ((rc = launch("prep", l, c.stream, [&] {
+                     launch_pdl(k_prep, pgrid, kThreads, 0, c.stream, ws, slot);
+                 })))
+                return rc;
+            if ((rc = launch("hist", l, c.stream, [&] {
+                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, 0);
+                 })))
+                return rc;
+            if ((rc = launch("classify", l, c.stream, [&] {
+                     launch_pdl(k_classify<KB>, cgrid, kThreads, 0, c.stream, ws, p, slot, l == L - 1);
+                 })))
+                return rc;
+            if ((rc = launch("ip_count", l, c.stream, [&] {
+                     launch_pdl(cfn, tgrid, kThreads, 0, c.stream, ws, p, slot, ip);
+                 })))
+                return rc;
+            if ((rc = launch("ip_scan", l, c.stream, [&] {
+                     launch_pdl(k_ip_scan_sums, sgrid, kThreads, 0, c.stream, ws, slot, ip);
+                     launch_pdl(k_ip_scan_blocks, 1, kThreads, 0, c.stream, ws, slot, ip);
+                     launch_pdl(k_ip_scan_apply, sgrid, kThreads, 0, c.stream, ws, slot, ip);
+                 })))
+                return rc;
+            if ((rc = launch("ip_swap", l, c.stream, [&] {
+                     launch_pdl(k_ip_swap<KB, VB>, wgrid, kThreads, 0, c.stream, ws, p, slot, ip);
+                 })))
+                return rc;
+        }
+    }
+    if ((rc = launch("bin_jobs", -1, c.stream, [&] {
+             launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
+                        c.stream, ws);
+         })))
+        return rc;
+    if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k0, v0, v0,
+                                             std::make_integer_sequence<int, FinishClasses<KB>::kCount>{})))
+        return rc;
+    auto lfn = k_finish_lsd<KB, VB>;
+    const size_t lsmem = sizeof(FinishLsdSmem<KB, VB>);
+    const int locc = kernel_ctas_per_sm((const void *)lfn, lsmem);
+    if ((rc = launch("finish_lsd", -1, c.stream, [&] {
+             launch_pdl(lfn, cap_grid((long long)sms * (locc > 0 ? locc : 1), c.n / 33 + 1), kThreads,
+                        lsmem, c.stream, ws, p, k0, k0, v0, v0);
+         })))
+        return rc;
+    return launch("copy", -1, c.stream, [&] {
+        launch_pdl(k_copy<KB, VB>, cap_grid(small_grid, max_tiles), kThreads, 0, c.stream, ws, kIpTile,
+                   k0, k0, v0, v0);
+    });
+}
+
 template <int KB, int VB>
 int run_call_vb(const Call &c) {
+    if (c.inplace) return run_inplace<KB, VB>(c);
     constexpr int STABLE = VB > 0;
     const int tv = c.pass_mode ? 0 : c.tile_variant;      // a single pass uses tile shape 0
     const int T = tv ? PartShape<KB, VB, 1>::kTile : PartShape<KB, VB, 0>::kTile;

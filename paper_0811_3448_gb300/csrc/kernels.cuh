@@ -493,10 +493,13 @@ static __global__ void k_prep(Ws ws, int slot) {
     if (nb == 0 || nb > ws.mcap || nt > ws.tcap) return;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
-    // cells: nt * kRadix words, as uint4
-    uint4 *cells4 = reinterpret_cast<uint4 *>(ws.cells);
-    const long long ncell4 = (long long)nt * kRadix / 4;
-    for (long long i = gtid; i < ncell4; i += gstride) cells4[i] = make_uint4(0, 0, 0, 0);
+    // cells: nt * kRadix words, as uint4 (none in the in-place mode, which
+    // has no look-back)
+    if (ws.cells) {
+        uint4 *cells4 = reinterpret_cast<uint4 *>(ws.cells);
+        const long long ncell4 = (long long)nt * kRadix / 4;
+        for (long long i = gtid; i < ncell4; i += gstride) cells4[i] = make_uint4(0, 0, 0, 0);
+    }
     uint4 *hist4 = reinterpret_cast<uint4 *>(ws.hist[slot]);
     const long long nhist4 = (long long)nb * kRadix / 4;
     for (long long i = gtid; i < nhist4; i += gstride) hist4[i] = make_uint4(0, 0, 0, 0);
@@ -840,7 +843,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
         sexcl[tid] = excl;
         ws.hist[slot][(size_t)b * kRadix + tid] = excl;
         const int cpos = bk.pos + p.bits;
-        const int cbuf = bk.buf ^ 1;
+        const int cbuf = p.inplace ? bk.buf : bk.buf ^ 1;
         const bool terminal = cpos >= W;
         const bool large = !terminal && cnt > (uint32_t)p.cutoff;
         const uint32_t tiles = large ? (cnt + T - 1) / T : 0;
@@ -1063,6 +1066,16 @@ __device__ __forceinline__ void bulk_load(void *dst, uintptr_t src, uint32_t byt
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+// A hint that brings [src, src + bytes) into L2 (16-byte aligned, a multiple
+// of 16 bytes), without waiting.
+__device__ __forceinline__ void l2_prefetch(uintptr_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+#ifndef BINAR_FIN_PF
+#define BINAR_FIN_PF 0
+#endif
+
 // Waits for phase `parity` of the barrier; false after limit_ns.
 __device__ __forceinline__ bool mbar_wait(void *bar, uint32_t parity, long long limit_ns) {
     const unsigned long long t0 = globaltimer_ns();
@@ -1286,7 +1299,9 @@ struct FinishSmem {
     uint32_t next_ticket;
     Job next_job;
     alignas(8) unsigned long long bar;     // mbarrier of the job's bulk copies
-    alignas(16) unsigned char keys[T * KB + 16];
+    // the job's keys (16 bytes of chunk slack), reused for the packed words of
+    // the in-run ranking, which read up to 3 words past the job's last one
+    alignas(16) unsigned char keys[T * KB + 32];
     alignas(16) unsigned char vals[VB ? T * VB + 16 : 16];
     uint16_t perm[T];
 };
@@ -1465,7 +1480,9 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
             // the bits above f are the job's common prefix
             const Bits pre = f ? (a & (KT::ones() << (W - f))) : (Bits)0;
             const Bits imask = ((Bits)1 << nidx) - 1;
-#pragma unroll
+            // no register arrays here: a loop unrolled twice keeps the code
+            // small (fully unrolled, instruction fetch stalled the warps)
+#pragma unroll 2
             for (int k = 0; k < IU; k++) {
                 const int x = k * kThreads + tid;
                 if (x < len) {
@@ -1476,7 +1493,7 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
                     int rank = 0;
 #pragma unroll
                     for (int t = 0; t < 4; t++) {
-                        const Bits py = sp[min(b0 + t, len - 1)];
+                        const Bits py = sp[b0 + t];        // b0 + 3 <= len + 2: in the buffer
                         rank += (t < m && py < px) ? 1 : 0;
                     }
                     for (int y = b0 + 4; y < b0 + m; y++) rank += sp[y] < px ? 1 : 0;
@@ -1609,7 +1626,25 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
         if (tid == 0) {   // the next job, while this one's data arrives
             const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
             s.next_ticket = t;
-            if (t < count) s.next_job = ws.jobs[mine[t]];
+            if (t < count) {
+                const Job nj = ws.jobs[mine[t]];
+                s.next_job = nj;
+#if BINAR_FIN_PF
+                // its chunks into L2 while this job is sorted
+                if (nj.pos < W && nj.len > 1 && nj.len <= kThreads * IU) {
+                    uintptr_t a0 = 0;
+                    uint32_t bytes = 0;
+                    chunk_range<KB>(reinterpret_cast<const Raw *>(nj.buf ? keys1 : keys0) + nj.begin,
+                                    (int)nj.len, &a0, &bytes);
+                    l2_prefetch(a0, bytes);
+                    if (VB) {
+                        chunk_range<VB>(reinterpret_cast<const V *>(nj.buf ? vals1 : vals0) + nj.begin,
+                                        (int)nj.len, &a0, &bytes);
+                        l2_prefetch(a0, bytes);
+                    }
+                }
+#endif
+            }
         }
         if (trivial) {
             if (len > kThreads * IU) {

@@ -81,7 +81,16 @@ inline int min_tile_for(int kb, int vb) {
     const int a = tile_for(kb, vb, 0), b = tile_for(kb, vb, 1);
     return a < b ? a : b;
 }
-inline int finish_cap_for(int kb) { return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048); }
+// (kernels.cuh TileShape): 8192 / 4096 / 2048 keys for 4 / 8 / 16-byte keys;
+// the default cutoff is the capacity
+inline int finish_cap_for(int kb, int vb) {
+    (void)vb;
+    return kb == 4 ? 8192 : (kb == 8 ? 4096 : 2048);
+}
+inline int default_cutoff(int kb, int vb, long long n) {
+    (void)n;
+    return finish_cap_for(kb, vb);
+}
 // partition levels of a sort that consumes `bits` key bits per pass
 inline int levels_for(int kb, int bits = kBits) { return (8 * kb + bits - 1) / bits; }
 
@@ -133,6 +142,65 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     return L;
 }
 
+// Workspace of the in-place mode (1-bit exchange passes, kIpTile-key tiles):
+// no second key / payload array and no look-back cells; per tile one marker
+// bit per key and four counters.  Capacities for the call's cutoff C: buckets
+// of a level are disjoint and hold more than C keys; every bucket of every
+// level yields at most two finisher jobs; reversed (copied) buckets are
+// disjoint and larger than C.
+struct InplaceLayout {
+    Layout base;
+    size_t mask, cnt, pre, bsum, total, first, end;
+    long long chunks;              // swap chunks per side (first[] entries per side)
+};
+
+inline InplaceLayout make_inplace_layout(long long n, int kb, int cutoff) {
+    constexpr long long T = 1024;                 // kIpTile
+    InplaceLayout L{};
+    const long long lv = 8LL * kb;                // one bit per level
+    const long long m = n / ((long long)cutoff + 1) + 2;
+    const long long t = n / T + m + 2;
+    long long j = 2 * lv * m + 2;
+    if (j > n / 2 + 2) j = n / 2 + 2;
+    const long long c = n / ((long long)cutoff + 1) + 2;
+    Layout &B = L.base;
+    B.mcap = (uint32_t)m;
+    B.tcap = (uint32_t)t;
+    B.jcap = (uint32_t)j;
+    B.ccap = (uint32_t)c;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    B.ctr = take(sizeof(Counters));
+    B.altk = take(0);
+    B.altv = take(0);
+    for (int s = 0; s < 2; s++) {
+        B.list[s] = take((size_t)m * sizeof(Bucket));
+        B.hist[s] = take((size_t)m * kRadix * sizeof(uint32_t));
+        B.andor[s] = take((size_t)m * 2 * sizeof(uint4));
+        B.order[s] = take((size_t)m * sizeof(uint32_t));
+    }
+    B.tilemap = take((size_t)t * sizeof(uint32_t));
+    B.cells = take(0);
+    B.jobs = take((size_t)j * sizeof(Job));
+    B.jobidx = take((size_t)j * sizeof(uint32_t));
+    B.jobs2 = take((size_t)j * sizeof(Job));
+    B.copies = take((size_t)c * sizeof(CopyJob));
+    L.mask = take((size_t)t * (T / 32) * 4);
+    L.cnt = take((size_t)t * 8);
+    L.pre = take((size_t)t * 8);
+    L.bsum = take((size_t)(t / (256 * 8) + 2) * 8);
+    L.total = take(16);
+    L.chunks = n / (2 * 1024) + 2;                // kIpChunk ranks per chunk; misplaced <= n / 2
+    L.first = take((size_t)L.chunks * 2 * 4);
+    B.total = o;
+    L.end = o;
+    return L;
+}
+
 inline Ws carve(const Layout &L, void *base) {
     unsigned char *b = static_cast<unsigned char *>(base);
     Ws ws{};
@@ -178,6 +246,7 @@ struct Call {
     int cutoff;
     int bits;                      // key bits per partition pass
     int tile_variant;              // 0 or 1 (PartShape TV)
+    bool inplace;                  // unstable in-place mode (1-bit exchange passes)
     int ctas_per_sm;
     long long timeout_ns;
     int skip_publish_tile;

@@ -128,7 +128,7 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     }
     Call c;
     std::memset(&c, 0, sizeof(c));
-    c.cutoff = finish_cap_for(key_bytes);
+    c.cutoff = finish_cap_for(key_bytes, val_bytes);
     c.bits = bits ? bits : kBits;
     c.tile_variant = 0;
     c.timeout_ns = 1000000000LL;

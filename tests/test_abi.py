@@ -146,3 +146,18 @@ def test_wide_keys_and_strings_argument_checks(lib):
         binding.ERR_INVALID_ARG
     assert f(aligned, aligned, 1000, 8, aligned, aligned, 16, None, None) == \
         binding.ERR_WORKSPACE_TOO_SMALL
+
+
+def test_inplace_argument_checks(lib):
+    aligned = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    f = lib.binar_sort_inplace
+    assert binding.inplace_workspace_bytes(1 << 20, 4, 4) < binding.workspace_bytes(1 << 20, 4, 4)
+    assert f(aligned, None, 10, 32, 3, 0, aligned, big, None, None) == binding.ERR_UNSUPPORTED
+    for cfg, rc in ((binding.Config(tile_keys=1024), binding.ERR_UNSUPPORTED),
+                    (binding.Config(bits_per_pass=8), binding.ERR_UNSUPPORTED),
+                    (binding.Config(small_cutoff=100), binding.ERR_INVALID_ARG)):
+        assert f(aligned, None, 10, 4, 0, 0, aligned, big, ctypes.byref(cfg), None) == rc
+    assert f(aligned, None, 100000, 4, 0, 0, aligned, 16, None, None) == \
+        binding.ERR_WORKSPACE_TOO_SMALL
+    assert f(aligned, aligned, 10, 4, 0, 0, aligned, big, None, None) == binding.ERR_INVALID_ARG

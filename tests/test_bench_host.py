@@ -43,6 +43,12 @@ def test_source_hash_ignores_comments_not_code(tmp_path):
         hashes[name] = b.kernel_source_hash()
     assert hashes["base"] == hashes["commented"]
     assert hashes["base"] != hashes["changed"]
+    # code outside the kernel files (the string levels, the C ABI) does not count
+    other, c4 = _tree(tmp_path, "other")
+    k = c4 / "strings.cu"
+    k.write_text(k.read_text() + "\nstatic int unrelated_code = 1;\n")
+    b.ROOT = str(other)
+    assert b.kernel_source_hash() == hashes["base"]
 
 
 def test_recorded_traffic_matches_widths_and_scales_per_record(tmp_path):

@@ -159,3 +159,4 @@ def test_repeated_calls_reuse_workspace():
     binding.check_status(ws)
     ek, ev = expect_pairs(keys, vals)
     assert same_bits(to_host(tk), ek) and same_bits(to_host(tv), ev)
+
