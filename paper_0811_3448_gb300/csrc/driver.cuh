@@ -83,6 +83,7 @@ int run_inplace(const Call &c) {
     ip.bsum = reinterpret_cast<uint32_t *>(wb + IL.bsum);
     ip.total = reinterpret_cast<unsigned long long *>(wb + IL.total);
     ip.first = reinterpret_cast<uint32_t *>(wb + IL.first);
+    ip.tinfo = reinterpret_cast<long long *>(wb + IL.tinfo);
     ip.chunk_cap = IL.chunks;
     Params p{};
     p.keys = c.keys;
@@ -113,9 +114,9 @@ int run_inplace(const Call &c) {
         const int hgrid = cap_grid((long long)sms * (hocc > 0 ? hocc : 1), max_tiles / kHistGroup + 1);
         const int pgrid = cap_grid(small_grid, max_buckets > max_tiles / 4 ? max_buckets : max_tiles / 4);
         const int cgrid = cap_grid(small_grid, max_buckets);
-        const int tgrid = cap_grid((long long)sms * 8, max_tiles);
+        const int tgrid = cap_grid((long long)sms * 8, max_tiles / kWarps + 1);   // a warp per tile
         const int sgrid = cap_grid(small_grid, max_tiles / kIpScanTile + 1);
-        const int wgrid = cap_grid(small_grid, c.n / (2LL * kIpChunk) + 1);
+        const int wgrid = cap_grid((long long)sms * 8, c.n / (2LL * kIpChunk) + 1);
         for (int l = 0; l < L; l++) {
             const int slot = l & 1;
             if ((rc = launch("prep", l, c.stream, [&] {

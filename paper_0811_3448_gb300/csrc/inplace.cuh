@@ -31,8 +31,8 @@
 
 namespace binar {
 
-constexpr int kIpTile = 1024;                 // keys per tile of the in-place passes
-constexpr int kIpWords = kIpTile / 32;        // marker words per tile
+constexpr int kIpTile = 4096;                 // keys per tile of the in-place passes
+constexpr int kIpWords = kIpTile / 32;        // marker words per tile (four per lane of a warp)
 constexpr int kIpChunk = 1024;                // exchanged pairs per swap work item
 constexpr int kIpScanItems = 8;
 constexpr int kIpScanTile = kThreads * kIpScanItems;   // tiles per scan block
@@ -45,6 +45,7 @@ struct IpWs {
     unsigned long long *total;   // [2]: misplaced keys of the level, left / right
     uint32_t *first;             // [2][chunk]: the tile holding the chunk's first rank, per side
     long long chunk_cap;         // entries per side of `first`
+    long long *tinfo;            // [tile][2]: the tile's first key position and its bucket's mid
 };
 
 // Bucket b's split point (its bit-0 keys come first): after classify, its
@@ -54,60 +55,65 @@ __device__ __forceinline__ long long ip_mid(const Ws &ws, int slot, uint32_t b, 
     return bk.begin + (long long)h[(size_t)b * kRadix + 1];
 }
 
+// One warp per tile, no block barriers: the warp loads BATCH words' keys at
+// once, ballots the misplaced bits, and lanes 0..BATCH-1 store the words.
 template <int KB, bool IDENT>
 __global__ void __launch_bounds__(kThreads) k_ip_count(Ws ws, Params p, int slot, IpWs ip) {
     pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
-    __shared__ uint32_t sc[2];
+    constexpr int BATCH = KB == 16 ? 8 : 16;
     if (has_error(ws.ctr)) return;
     const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     const Bucket *list = slot ? ws.list[1] : ws.list[0];
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
-    const uint32_t nt = (uint32_t)(alloc >> 32);
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const long long nt = (long long)(alloc >> 32);
+    const int lane = threadIdx.x & 31;
     const Raw *keys = reinterpret_cast<const Raw *>(p.keys);
-    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    const long long nw = (long long)gridDim.x * kWarps;
+    for (long long t = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); t < nt; t += nw) {
         const uint32_t b = ws.tilemap[t];
         const Bucket bk = list[b];
-        if (tid < 2) sc[tid] = 0;
-        __syncthreads();
         uint32_t cl = 0, cr = 0;
+        long long tb = 0, mid = 0;
+        uint32_t *mw = ip.mask + (size_t)t * kIpWords;
         if (!(bk.flags & kSkip)) {
-            const long long tb = bk.begin + (long long)(t - bk.tile_start) * kIpTile;
+            tb = bk.begin + (t - (long long)bk.tile_start) * kIpTile;
             const int tlen = (int)min((long long)kIpTile, bk.begin + (long long)bk.len - tb);
-            const long long mid = ip_mid(ws, slot, b, bk);
+            mid = ip_mid(ws, slot, b, bk);
+            for (int w0 = 0; w0 < kIpWords; w0 += BATCH) {
+                Raw kx[BATCH];
 #pragma unroll
-            for (int q = 0; q < kIpWords / kWarps; q++) {
-                const int wi = w * (kIpWords / kWarps) + q;
-                const int i = wi * 32 + lane;
-                const bool valid = i < tlen;
-                const long long at = tb + i;
-                bool mis = false, left = false;
-                if (valid) {
-                    const uint32_t bit = KT::bits_at(enc(keys[at]), bk.pos, 1);
-                    left = at < mid;
-                    mis = left ? bit != 0 : bit == 0;
+                for (int q = 0; q < BATCH; q++) {
+                    const int i = (w0 + q) * 32 + lane;
+                    kx[q] = i < tlen ? keys[tb + i] : Raw{};
                 }
-                const uint32_t word = __ballot_sync(0xffffffffu, mis);
-                const uint32_t lw = __ballot_sync(0xffffffffu, left);
-                if (lane == 0) ip.mask[(size_t)t * kIpWords + wi] = word;
-                cl += __popc(word & lw);
-                cr += __popc(word & ~lw);
+                uint32_t mine = 0;
+#pragma unroll
+                for (int q = 0; q < BATCH; q++) {
+                    const int i = (w0 + q) * 32 + lane;
+                    const bool valid = i < tlen;
+                    const bool left = valid && tb + i < mid;
+                    const uint32_t bit = KT::bits_at(enc(kx[q]), bk.pos, 1);
+                    const bool mis = valid && (left ? bit != 0 : bit == 0);
+                    const uint32_t word = __ballot_sync(0xffffffffu, mis);
+                    const uint32_t lw = __ballot_sync(0xffffffffu, left);
+                    if (lane == q) mine = word;
+                    cl += __popc(word & lw);
+                    cr += __popc(word & ~lw);
+                }
+                if (lane < BATCH) mw[w0 + lane] = mine;
             }
-            if (lane == 0) {
-                atomicAdd(&sc[0], cl);
-                atomicAdd(&sc[1], cr);
-            }
-        } else if (tid < kIpWords) {
-            ip.mask[(size_t)t * kIpWords + tid] = 0u;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kIpWords / 32; q++) mw[q * 32 + lane] = 0u;
         }
-        __syncthreads();
-        if (tid == 0) {
-            ip.cnt[2 * (size_t)t] = sc[0];
-            ip.cnt[2 * (size_t)t + 1] = sc[1];
+        if (lane == 0) {
+            ip.cnt[2 * t] = cl;
+            ip.cnt[2 * t + 1] = cr;
+            ip.tinfo[2 * t] = tb;
+            ip.tinfo[2 * t + 1] = mid;
         }
-        __syncthreads();
     }
 }
 
@@ -205,18 +211,19 @@ static __global__ void __launch_bounds__(kThreads) k_ip_scan_apply(Ws ws, int sl
 }
 
 // Exchanges the k-th misplaced key left of mid with the k-th right of it,
-// chunk by chunk of ranks.  Positions are taken from the marker bits; a
-// chunk's positions start as -1 and a pair with a missing or foreign position
-// is reported (BINAR_ERR_DEVICE_BOUNDS) and skipped.
+// chunk by chunk of ranks.  Positions are taken from the marker bits (a warp
+// per tile, four words per lane); a chunk's positions start as -1 and a pair
+// with a missing or foreign position is reported (BINAR_ERR_DEVICE_BOUNDS)
+// and skipped.  Each thread loads its pairs before storing them.
 template <int KB, int VB>
 __global__ void __launch_bounds__(kThreads) k_ip_swap(Ws ws, Params p, int slot, IpWs ip) {
     pdl_entry();
     using Raw = typename KeyTraits<KB>::Raw;
     using V = typename ValTraits<VB>::T;
+    constexpr int PER = kIpChunk / kThreads;              // pairs per thread
     __shared__ long long pos[2][kIpChunk];
     __shared__ uint32_t sfirst;
     if (has_error(ws.ctr)) return;
-    const Bucket *list = slot ? ws.list[1] : ws.list[0];
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
     const unsigned long long mtot = ip.total[0];
@@ -243,22 +250,21 @@ __global__ void __launch_bounds__(kThreads) k_ip_swap(Ws ws, Params p, int slot,
                 const uint32_t t = base + w;
                 if (t < nt) {
                     const unsigned long long r0 = ip.pre[2 * (size_t)t + side];
-                    const uint32_t b = ws.tilemap[t];
-                    const Bucket bk = list[b];
-                    uint32_t bits = 0;
+                    uint32_t bits[4] = {0u, 0u, 0u, 0u};
                     long long wb = 0;
-                    if (r0 < hi && !(bk.flags & kSkip)) {
-                        const long long tb = bk.begin + (long long)(t - bk.tile_start) * kIpTile;
-                        const long long mid = ip_mid(ws, slot, b, bk);
-                        wb = tb + lane * 32;
-                        bits = ip.mask[(size_t)t * kIpWords + lane];
-                        // keep the bits of this side of mid
-                        const long long cut = mid - wb;            // bits below cut are left of mid
-                        const uint32_t lowmask = cut >= 32 ? 0xffffffffu
-                                                           : (cut <= 0 ? 0u : ((1u << cut) - 1u));
-                        bits &= side == 0 ? lowmask : ~lowmask;
+                    if (r0 < hi) {       // a skipped bucket's tiles have no marker bits
+                        const long long tb = ip.tinfo[2 * (size_t)t], mid = ip.tinfo[2 * (size_t)t + 1];
+                        const uint4 mw = reinterpret_cast<const uint4 *>(ip.mask + (size_t)t * kIpWords)[lane];
+                        bits[0] = mw.x; bits[1] = mw.y; bits[2] = mw.z; bits[3] = mw.w;
+                        wb = tb + (long long)lane * 128;
+#pragma unroll
+                        for (int k = 0; k < 4; k++) {     // keep the bits of this side of mid
+                            const long long cut = mid - (wb + 32 * k);
+                            const uint32_t low = cut >= 32 ? 0xffffffffu : (cut <= 0 ? 0u : ((1u << cut) - 1u));
+                            bits[k] &= side == 0 ? low : ~low;
+                        }
                     }
-                    const uint32_t cntb = __popc(bits);
+                    const uint32_t cntb = __popc(bits[0]) + __popc(bits[1]) + __popc(bits[2]) + __popc(bits[3]);
                     uint32_t incl = cntb;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
@@ -266,30 +272,56 @@ __global__ void __launch_bounds__(kThreads) k_ip_swap(Ws ws, Params p, int slot,
                         if (lane >= o) incl += y;
                     }
                     unsigned long long r = r0 + incl - cntb;
-                    while (bits) {
-                        const int j = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        if (r >= lo && r < hi) pos[side][r - lo] = wb + j;
-                        r++;
+#pragma unroll
+                    for (int k = 0; k < 4; k++) {
+                        uint32_t x = bits[k];
+                        while (x) {
+                            const int j = __ffs(x) - 1;
+                            x &= x - 1;
+                            if (r >= lo && r < hi) pos[side][r - lo] = wb + 32 * k + j;
+                            r++;
+                        }
                     }
                 }
             }
             __syncthreads();
         }
         const int m = (int)(hi - lo);
-        for (int j = tid; j < m; j += kThreads) {
-            const long long a = pos[0][j], z = pos[1][j];
-            if (a < 0 || z < 0 || a >= p.n || z >= p.n || a >= z) {
-                set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-                continue;
+        long long a[PER], z[PER];
+        bool ok[PER];
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int j = q * kThreads + tid;
+            ok[q] = false;
+            if (j < m) {
+                a[q] = pos[0][j];
+                z[q] = pos[1][j];
+                ok[q] = a[q] >= 0 && z[q] >= 0 && a[q] < p.n && z[q] < p.n && a[q] < z[q];
+                if (!ok[q]) set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
             }
-            const Raw ka = keys[a];
-            keys[a] = keys[z];
-            keys[z] = ka;
-            if (VB) {
-                const V va = vals[a];
-                vals[a] = vals[z];
-                vals[z] = va;
+        }
+        Raw ka[PER], kz[PER];
+        V va[PER], vz[PER];
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (ok[q]) {
+                ka[q] = keys[a[q]];
+                kz[q] = keys[z[q]];
+                if (VB) {
+                    va[q] = vals[a[q]];
+                    vz[q] = vals[z[q]];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            if (ok[q]) {
+                keys[a[q]] = kz[q];
+                keys[z[q]] = ka[q];
+                if (VB) {
+                    vals[a[q]] = vz[q];
+                    vals[z[q]] = va[q];
+                }
             }
         }
         __syncthreads();

@@ -1066,16 +1066,6 @@ __device__ __forceinline__ void bulk_load(void *dst, uintptr_t src, uint32_t byt
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-// A hint that brings [src, src + bytes) into L2 (16-byte aligned, a multiple
-// of 16 bytes), without waiting.
-__device__ __forceinline__ void l2_prefetch(uintptr_t src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
-#ifndef BINAR_FIN_PF
-#define BINAR_FIN_PF 0
-#endif
-
 // Waits for phase `parity` of the barrier; false after limit_ns.
 __device__ __forceinline__ bool mbar_wait(void *bar, uint32_t parity, long long limit_ns) {
     const unsigned long long t0 = globaltimer_ns();
@@ -1626,25 +1616,7 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
         if (tid == 0) {   // the next job, while this one's data arrives
             const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
             s.next_ticket = t;
-            if (t < count) {
-                const Job nj = ws.jobs[mine[t]];
-                s.next_job = nj;
-#if BINAR_FIN_PF
-                // its chunks into L2 while this job is sorted
-                if (nj.pos < W && nj.len > 1 && nj.len <= kThreads * IU) {
-                    uintptr_t a0 = 0;
-                    uint32_t bytes = 0;
-                    chunk_range<KB>(reinterpret_cast<const Raw *>(nj.buf ? keys1 : keys0) + nj.begin,
-                                    (int)nj.len, &a0, &bytes);
-                    l2_prefetch(a0, bytes);
-                    if (VB) {
-                        chunk_range<VB>(reinterpret_cast<const V *>(nj.buf ? vals1 : vals0) + nj.begin,
-                                        (int)nj.len, &a0, &bytes);
-                        l2_prefetch(a0, bytes);
-                    }
-                }
-#endif
-            }
+            if (t < count) s.next_job = ws.jobs[mine[t]];
         }
         if (trivial) {
             if (len > kThreads * IU) {

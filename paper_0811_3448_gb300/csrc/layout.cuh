@@ -144,18 +144,18 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
 
 // Workspace of the in-place mode (1-bit exchange passes, kIpTile-key tiles):
 // no second key / payload array and no look-back cells; per tile one marker
-// bit per key and four counters.  Capacities for the call's cutoff C: buckets
+// bit per key, four counters and its first position and split point.  Capacities for the call's cutoff C: buckets
 // of a level are disjoint and hold more than C keys; every bucket of every
 // level yields at most two finisher jobs; reversed (copied) buckets are
 // disjoint and larger than C.
 struct InplaceLayout {
     Layout base;
-    size_t mask, cnt, pre, bsum, total, first, end;
+    size_t mask, cnt, pre, bsum, total, first, tinfo, end;
     long long chunks;              // swap chunks per side (first[] entries per side)
 };
 
 inline InplaceLayout make_inplace_layout(long long n, int kb, int cutoff) {
-    constexpr long long T = 1024;                 // kIpTile
+    constexpr long long T = 4096;                 // kIpTile
     InplaceLayout L{};
     const long long lv = 8LL * kb;                // one bit per level
     const long long m = n / ((long long)cutoff + 1) + 2;
@@ -196,6 +196,7 @@ inline InplaceLayout make_inplace_layout(long long n, int kb, int cutoff) {
     L.total = take(16);
     L.chunks = n / (2 * 1024) + 2;                // kIpChunk ranks per chunk; misplaced <= n / 2
     L.first = take((size_t)L.chunks * 2 * 4);
+    L.tinfo = take((size_t)t * 16);
     B.total = o;
     L.end = o;
     return L;
