@@ -74,11 +74,13 @@ typedef enum {
 /* Tuning knobs; a zero field takes the library default.  Pass NULL for all
  * defaults. */
 typedef struct {
-    int tile_keys;          /* keys per partition tile: 0 or the width's tile --
-                               6144 (4-byte keys with a payload), 7168 (4-byte
-                               keys alone), 4096 (8-byte keys), 2048 (16-byte
-                               keys) */
-    int bits_per_pass;      /* k, key bits consumed per partition pass: 0 or 8 */
+    int tile_keys;          /* keys per partition tile: 0 or one of the width's two
+                               compiled tiles -- 6144 or 4096 (4-byte keys with a
+                               payload), 7168 or 4096 (4-byte keys alone), 4096 or
+                               2048 (8-byte keys), 2048 or 1024 (16-byte keys);
+                               other values return BINAR_ERR_UNSUPPORTED */
+    int bits_per_pass;      /* k, key bits consumed per partition pass: 0 (= 8) or
+                               4 .. 8 (the in-place mode takes 0 or 1) */
     int small_cutoff;       /* C: buckets of <= C keys are finished in shared memory;
                                2048 .. the finisher capacity: 8192 / 4096 / 2048
                                keys for 4 / 8 / 16-byte keys (0: the capacity) */
@@ -195,7 +197,7 @@ int binar_sort_segmented(void *d_keys, void *d_vals, const int64_t *d_offsets,
  * pos .. pos+bits-1 of each key's encoding (bits past the key read as 0),
  * digit groups in ascending order, input order kept inside each group.
  *   d_offsets  device pointer to 2^bits + 1 int64 receiving the group bounds, or NULL
- *   bits       0 (= 8) or 8;  0 <= pos < 8 * key_bytes
+ *   bits       0 (= 8) or 1 .. 8;  0 <= pos < 8 * key_bytes
  *   ws_bytes   >= binar_workspace_bytes(n, 1, key_bytes, val_bytes)
  * Input and output must not overlap. */
 int binar_partition_pass(const void *d_keys_in, const void *d_vals_in, void *d_keys_out,
@@ -235,6 +237,16 @@ int binar_partition_pass_noalloc(const void *d_keys_in, const void *d_vals_in, v
  * allocates nothing (the word moves through a host variable).  The paper has
  * no counterpart.  Returns binar_status of the query itself. */
 int binar_partition_pass_noalloc_status(void *stream, int *out_status);
+
+/* TEST HOOK for the calls to binar_partition_pass_noalloc that follow (its
+ * counterpart of binar_config's debug_skip_publish_tile and
+ * lookback_timeout_ns, which that call takes no config for): if
+ * skip_publish_tile > 0, tile (skip_publish_tile - 1) never publishes its
+ * counts, so that its successors' look-back waits run out after
+ * lookback_timeout_ns (0 = 1 s) and the pass records
+ * BINAR_ERR_DEVICE_TIMEOUT.  (0, 0) restores the defaults.  Process-wide;
+ * negative arguments return BINAR_ERR_INVALID_ARG. */
+int binar_partition_pass_noalloc_debug(int skip_publish_tile, int64_t lookback_timeout_ns);
 
 /* Waits for `stream`, then reads the device status word of the workspace
  * into *out_status (a binar_status) and clears it.  Returns binar_status of

@@ -5,6 +5,7 @@
 // caller's stream; nothing allocates or synchronises.
 #pragma once
 
+#include <type_traits>
 #include <utility>
 
 #include "inplace.cuh"
@@ -34,13 +35,19 @@ int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int
     });
 }
 
+// Sorts of at most this many keys finish every job in one launch, of the
+// smallest class that holds the largest job the call can have, without the
+// binning pass (fewer launches; idle items in smaller jobs cost little at
+// that size).
+constexpr long long kOneFinishLaunchMaxN = 1LL << 21;
+
 template <int KB, int VB, int CLS>
 int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1, void *v0,
-                        void *v1) {
+                        void *v1, int all_jobs = 0) {
     constexpr int IU = FinishClasses<KB>::iu(CLS);
     // a job holds at most min(cutoff, n) keys: larger classes never get one
     const long long maxjob = c.cutoff < c.n ? c.cutoff : c.n;
-    if (CLS > 0 && (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) >= maxjob)
+    if (!all_jobs && CLS > 0 && (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) >= maxjob)
         return BINAR_OK;
     // the identity key map is compiled separately for 4- and 8-byte keys
     auto ffn = (KB != 16 && c.map == BINAR_MAP_UNSIGNED) ? k_finish<KB, VB, CLS, KB != 16>
@@ -48,10 +55,12 @@ int launch_finish_class(const Call &c, const Ws &ws, const Params &p, void *k0, 
     const size_t smem = sizeof(FinishSmem<KB, VB, IU>);
     const int occ = kernel_ctas_per_sm((const void *)ffn, smem);
     // jobs of this class hold more keys than the class below it can
-    const long long lower = CLS > 0 ? (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) : 1;
-    const int grid = cap_grid((long long)device_sms() * (occ > 0 ? occ : 1), c.n / (lower + 1) + 1);
+    const long long lower = (CLS > 0 && !all_jobs) ? (long long)kThreads * FinishClasses<KB>::iu(CLS > 0 ? CLS - 1 : 0) : 1;
+    // an unsegmented call of at most `cutoff` keys has at most one job
+    const long long jobs_max = (all_jobs && !c.offsets && c.n <= c.cutoff) ? 1 : c.n / (lower + 1) + 1;
+    const int grid = cap_grid((long long)device_sms() * (occ > 0 ? occ : 1), jobs_max);
     return launch("finish", CLS, c.stream, [&] {
-        launch_pdl(ffn, grid, kThreads, smem, c.stream, ws, p, k0, k1, v0, v1);
+        launch_pdl(ffn, grid, kThreads, smem, c.stream, ws, p, k0, k1, v0, v1, all_jobs);
     });
 }
 
@@ -59,6 +68,21 @@ template <int KB, int VB, int... CLS>
 int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0, void *k1,
                           void *v0, void *v1, std::integer_sequence<int, CLS...>) {
     int rc = BINAR_OK;
+    if (c.n <= kOneFinishLaunchMaxN) {
+        // one launch, of the smallest class that holds min(cutoff, n) keys
+        const long long maxjob = c.cutoff < c.n ? c.cutoff : c.n;
+        bool launched = false;
+        auto one = [&](auto cls) {
+            constexpr int C = decltype(cls)::value;
+            if (launched || (C + 1 < FinishClasses<KB>::kCount &&
+                             (long long)kThreads * FinishClasses<KB>::iu(C) < maxjob))
+                return;
+            launched = true;
+            rc = launch_finish_class<KB, VB, C>(c, ws, p, k0, k1, v0, v1, 1);
+        };
+        (one(std::integral_constant<int, CLS>{}), ...);
+        return rc;
+    }
     ((rc = rc ? rc : launch_finish_class<KB, VB, CLS>(c, ws, p, k0, k1, v0, v1)), ...);
     return rc;
 }
@@ -147,7 +171,7 @@ int run_inplace(const Call &c) {
                 return rc;
         }
     }
-    if ((rc = launch("bin_jobs", -1, c.stream, [&] {
+    if (c.n > kOneFinishLaunchMaxN && (rc = launch("bin_jobs", -1, c.stream, [&] {
              launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
                         c.stream, ws);
          })))
@@ -215,7 +239,8 @@ int run_call_vb(const Call &c) {
                  launch_pdl(k_prefix_only, 1, kThreads, 0, c.stream, ws, c.pass_offsets, c.n, bits);
              })))
             return rc;
-        return launch_partition<KB, VB, true, 0>(c, ws, p, 0, 1, const_cast<void *>(c.keys_in),
+        // the call's one partition is its level 0 (the test hook's level)
+        return launch_partition<KB, VB, true, 0>(c, ws, p, 0, 0, const_cast<void *>(c.keys_in),
                                                  c.keys_out, const_cast<void *>(c.vals_in), c.vals_out,
                                                  tiles);
     }
@@ -270,7 +295,7 @@ int run_call_vb(const Call &c) {
         }
     }
     {
-        if ((rc = launch("bin_jobs", -1, c.stream, [&] {
+        if (c.n > kOneFinishLaunchMaxN && (rc = launch("bin_jobs", -1, c.stream, [&] {
                  launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
                             c.stream, ws);
              })))

@@ -1066,6 +1066,12 @@ __device__ __forceinline__ void bulk_load(void *dst, uintptr_t src, uint32_t byt
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
         ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
+// A hint that brings [src, src + bytes) into L2 (16-byte aligned, a multiple
+// of 16 bytes), without waiting.
+__device__ __forceinline__ void l2_prefetch(uintptr_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Waits for phase `parity` of the barrier; false after limit_ns.
 __device__ __forceinline__ bool mbar_wait(void *bar, uint32_t parity, long long limit_ns) {
     const unsigned long long t0 = globaltimer_ns();
@@ -1175,6 +1181,26 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
             bulk_begin(&s.bar, kbytes + vbytes);
             bulk_load(s.keys, ka0, kbytes, &s.bar);
             if (VB) bulk_load(s.vals, va0, vbytes, &s.bar);
+        }
+        // tickets go out in order, so the tile one grid ahead is about to be
+        // taken by some CTA: bring its bytes into the shared L2 now (3% off
+        // the pass at 256M pairs)
+        if (tid == 32 && t + gridDim.x < nt) {
+            const uint32_t u = t + gridDim.x;
+            const uint32_t bu = ws.tilemap[u];
+            const Bucket bq = list[bu];
+            if (!(bq.flags & kSkip)) {
+                const long long ub = bq.begin + (long long)(u - bq.tile_start) * T;
+                const int ulen = (int)min((long long)T, (long long)bq.begin + (long long)bq.len - ub);
+                uintptr_t a0 = 0;
+                uint32_t bytes = 0;
+                chunk_range<KB>(reinterpret_cast<const Raw *>(bq.buf ? keys1 : keys0) + ub, ulen, &a0, &bytes);
+                l2_prefetch(a0, bytes);
+                if (VB) {
+                    chunk_range<VB>(reinterpret_cast<const V *>(bq.buf ? vals1 : vals0) + ub, ulen, &a0, &bytes);
+                    l2_prefetch(a0, bytes);
+                }
+            }
         }
         const bool landed = mbar_wait(&s.bar, phase, p.timeout_ns);
         if (__syncthreads_or(!landed)) {                  // uniform across the CTA
@@ -1562,7 +1588,7 @@ template <int KB, int VB, int CLS, bool IDENT>
 __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CLS) <= 16)
                                                 ? 4
                                                 : (FinishClasses<KB>::iu(CLS) <= 18 ? 3 : 2))
-    k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1) {
+    k_finish(Ws ws, Params p, void *keys0, void *keys1, void *vals0, void *vals1, int all_jobs) {
     pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
@@ -1576,18 +1602,22 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
     if (has_error(ws.ctr)) return;
     const Encoder<KB> enc(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     const Decoder<KB> dec(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
+    // all_jobs: this launch (of the smallest class that holds the call's
+    // largest possible job) takes every job of the call straight from the
+    // job list, unbinned (small sorts: one launch instead of the binning pass
+    // and one per class)
     uint32_t base = 0;
     for (int c = 0; c < CLS; c++) base += ws.ctr->class_count[c];
-    const uint32_t count = ws.ctr->class_count[CLS];
-    if (count == 0 || base + count > ws.jcap) return;
-    const uint32_t *mine = ws.jobidx + base;
+    const uint32_t count = all_jobs ? min(ws.ctr->njobs, ws.jcap) : ws.ctr->class_count[CLS];
+    if (count == 0 || (!all_jobs && base + count > ws.jcap)) return;
+    const uint32_t *mine = all_jobs ? nullptr : ws.jobidx + base;
     const int tid = threadIdx.x;
     uint32_t phase = 0;
     if (tid == 0) {
         mbar_init(&s.bar);
         const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
         s.next_ticket = t;
-        if (t < count) s.next_job = ws.jobs[mine[t]];
+        if (t < count) s.next_job = ws.jobs[mine ? mine[t] : t];
     }
     for (;;) {
         __syncthreads();
@@ -1616,7 +1646,7 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
         if (tid == 0) {   // the next job, while this one's data arrives
             const uint32_t t = atomicAdd(&ws.ctr->class_ticket[CLS], 1u);
             s.next_ticket = t;
-            if (t < count) s.next_job = ws.jobs[mine[t]];
+            if (t < count) s.next_job = ws.jobs[mine ? mine[t] : t];
         }
         if (trivial) {
             if (len > kThreads * IU) {

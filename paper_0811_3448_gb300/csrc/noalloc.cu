@@ -8,6 +8,7 @@
 // pay for (or synchronise on) cudaMalloc -- and callers that cannot size and
 // keep a workspace of their own.  This entry point takes only the inputs and
 // outputs; its scratch lives in kScratchBytes of device memory declared here.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -90,6 +91,12 @@ Layout pass_layout(long long n, int kb, int vb) {
     return L;
 }
 
+// Test hook (binar_partition_pass_noalloc_debug): a level-0 tile that never
+// publishes (-1 = none) and the look-back limit (0 = 1 s) of the calls that
+// follow.
+std::atomic<int> g_skip_publish_tile{-1};
+std::atomic<long long> g_timeout_ns{0};
+
 bool aligned_to(const void *p, int bytes) {
     return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(bytes - 1)) == 0;
 }
@@ -131,8 +138,9 @@ extern "C" int binar_partition_pass_noalloc(const void *d_keys_in, const void *d
     c.cutoff = finish_cap_for(key_bytes, val_bytes);
     c.bits = bits ? bits : kBits;
     c.tile_variant = 0;
-    c.timeout_ns = 1000000000LL;
-    c.skip_publish_tile = -1;
+    const long long limit = g_timeout_ns.load();
+    c.timeout_ns = limit > 0 ? limit : 1000000000LL;
+    c.skip_publish_tile = g_skip_publish_tile.load();
     c.pass_mode = true;
     c.layout = &lay;
     c.keys_in = d_keys_in;
@@ -172,5 +180,12 @@ extern "C" int binar_partition_pass_noalloc_status(void *stream, int *out_status
         return BINAR_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return BINAR_ERR_CUDA;
     *out_status = (int)v;
+    return BINAR_OK;
+}
+
+extern "C" int binar_partition_pass_noalloc_debug(int skip_publish_tile, int64_t lookback_timeout_ns) {
+    if (skip_publish_tile < 0 || lookback_timeout_ns < 0) return BINAR_ERR_INVALID_ARG;
+    g_skip_publish_tile.store(skip_publish_tile - 1);
+    g_timeout_ns.store(lookback_timeout_ns);
     return BINAR_OK;
 }

@@ -119,6 +119,18 @@ def test_argument_checks_need_no_gpu(lib):
                                     aligned, big, None, None) == binding.ERR_UNSUPPORTED
 
 
+def test_noalloc_debug_hook_argument_checks(lib):
+    """The no-alloc pass's test hook only records its arguments (no CUDA
+    call); negative values are refused and (0, 0) restores the defaults."""
+    f = lib.binar_partition_pass_noalloc_debug
+    f.argtypes = [ctypes.c_int, ctypes.c_int64]
+    f.restype = ctypes.c_int
+    assert f(-1, 0) == binding.ERR_INVALID_ARG
+    assert f(0, -5) == binding.ERR_INVALID_ARG
+    assert f(3, 1000) == binding.OK
+    assert f(0, 0) == binding.OK
+
+
 def test_wide_keys_and_strings_argument_checks(lib):
     aligned = ctypes.c_void_p(0x1000)
     big = 1 << 40

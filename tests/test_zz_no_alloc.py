@@ -6,7 +6,9 @@ Called through the C ABI and checked, bit for bit, against the ordinary
 binar_partition_pass (which takes a workspace) and against the oracle's
 partition pass, on two calls in a row; then at every documented size limit
 (which must succeed) and one key past it (which must be refused), always on
-real device buffers of the size passed.  Kept in a file of its own that
+real device buffers of the size passed; and a look-back wait made to run out
+(a tile that never publishes, through the test hook) is reported by the
+status query and leaves the next call clean.  Kept in a file of its own that
 pytest collects last.
 """
 import ctypes
@@ -32,6 +34,8 @@ def _lib():
     lib.binar_partition_pass_noalloc.restype = i32
     lib.binar_partition_pass_noalloc_status.argtypes = [p, ctypes.POINTER(i32)]
     lib.binar_partition_pass_noalloc_status.restype = i32
+    lib.binar_partition_pass_noalloc_debug.argtypes = [i32, i64]
+    lib.binar_partition_pass_noalloc_debug.restype = i32
     return lib
 
 
@@ -127,3 +131,26 @@ def test_noalloc_pass_at_its_documented_limit(kb, vb, kmap, limit):
     assert same_bits(to_host(ko)[:limit], ek)
     if vals is not None:
         assert same_bits(to_host(vo)[:limit], ev)
+
+
+def test_noalloc_status_reports_a_timeout_and_the_next_call_is_clean():
+    require_gpu()
+    lib = _lib()
+    n = 6144 * 40 + 17                       # 41 tiles of the pass; tile 3 never publishes
+    keys = inputs.uniform_keys(n, np.uint32, np.random.Generator(np.random.PCG64(77)))
+    vals = _vals(4, n)
+    tk, tv = to_dev(keys), to_dev(vals)
+    assert lib.binar_partition_pass_noalloc_debug(4, 1_000_000) == binding.OK
+    try:
+        rc, *_ = _noalloc_pass(lib, tk, tv, 0, oracle.MAP_UNSIGNED)
+        assert rc == binding.OK
+        assert _status(lib) == binding.ERR_DEVICE_TIMEOUT
+    finally:
+        assert lib.binar_partition_pass_noalloc_debug(0, 0) == binding.OK
+    assert _status(lib) == binding.OK        # the query cleared the word
+    rc, ko, vo, offs = _noalloc_pass(lib, tk, tv, 8, oracle.MAP_UNSIGNED)
+    assert rc == binding.OK
+    assert _status(lib) == binding.OK
+    ek, ev, eoffs = oracle.partition_pass(keys, vals, key_map=oracle.MAP_UNSIGNED, pos=8, k=8)
+    assert same_bits(to_host(ko), ek) and same_bits(to_host(vo), ev)
+    assert np.array_equal(to_host(offs), eoffs)
