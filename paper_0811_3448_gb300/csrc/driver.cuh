@@ -21,6 +21,14 @@ inline int cap_grid(long long grid, long long work) {
     return (int)(grid < work ? grid : work);
 }
 
+// Tiles per histogram ticket for a level of at most `tiles` tiles on a
+// persistent grid of `full` CTAs: kHistGroup once every CTA gets a group,
+// fewer below that (down to one tile per ticket).
+inline int hist_group(long long tiles, long long full) {
+    const long long g = tiles / (full > 0 ? full : 1);
+    return (int)(g < 1 ? 1 : (g > kHistGroup ? kHistGroup : g));
+}
+
 template <int KB, int VB, bool STABLE, int TV>
 int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int level,
                      void *k0, void *k1, void *v0, void *v1, long long max_tiles) {
@@ -135,7 +143,9 @@ int run_inplace(const Call &c) {
         auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
         auto cfn = c.map == BINAR_MAP_UNSIGNED ? k_ip_count<KB, true> : k_ip_count<KB, false>;
         const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
-        const int hgrid = cap_grid((long long)sms * (hocc > 0 ? hocc : 1), max_tiles / kHistGroup + 1);
+        const long long hfull = (long long)sms * (hocc > 0 ? hocc : 1);
+        const int hgroup = hist_group(max_tiles, hfull);
+        const int hgrid = cap_grid(hfull, max_tiles / hgroup + 1);
         const int pgrid = cap_grid(small_grid, max_buckets > max_tiles / 4 ? max_buckets : max_tiles / 4);
         const int cgrid = cap_grid(small_grid, max_buckets);
         const int tgrid = cap_grid((long long)sms * 8, max_tiles / kWarps + 1);   // a warp per tile
@@ -148,7 +158,7 @@ int run_inplace(const Call &c) {
                  })))
                 return rc;
             if ((rc = launch("hist", l, c.stream, [&] {
-                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, 0);
+                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, hgroup);
                  })))
                 return rc;
             if ((rc = launch("classify", l, c.stream, [&] {
@@ -229,9 +239,11 @@ int run_call_vb(const Call &c) {
         {
             auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
             const int occ = kernel_ctas_per_sm((const void *)hfn, 0);
-            const int hg = cap_grid((long long)sms * (occ > 0 ? occ : 1), tiles / kHistGroup + 1);
+            const long long hfull = (long long)sms * (occ > 0 ? occ : 1);
+            const int hgroup = hist_group(tiles, hfull);
+            const int hg = cap_grid(hfull, tiles / hgroup + 1);
             if ((rc = launch("hist", 0, c.stream, [&] {
-                     launch_pdl(hfn, hg, kThreads, 0, c.stream, ws, p, 0, 0);
+                     launch_pdl(hfn, hg, kThreads, 0, c.stream, ws, p, 0, hgroup);
                  })))
                 return rc;
         }
@@ -272,7 +284,9 @@ int run_call_vb(const Call &c) {
     if (seg || c.n > c.cutoff) {
         auto hfn = c.map == BINAR_MAP_UNSIGNED ? k_hist<KB, true> : k_hist<KB, false>;
         const int hocc = kernel_ctas_per_sm((const void *)hfn, 0);
-        const int hgrid = cap_grid((long long)sms * (hocc > 0 ? hocc : 1), max_tiles / kHistGroup + 1);
+        const long long hfull = (long long)sms * (hocc > 0 ? hocc : 1);
+        const int hgroup = hist_group(max_tiles, hfull);
+        const int hgrid = cap_grid(hfull, max_tiles / hgroup + 1);
         const int pgrid = cap_grid(small_grid, max_buckets > max_tiles / 4 ? max_buckets : max_tiles / 4);
         const int cgrid = cap_grid(small_grid, max_buckets);
         for (int l = 0; l < L; l++) {
@@ -282,7 +296,7 @@ int run_call_vb(const Call &c) {
                  })))
                 return rc;
             if ((rc = launch("hist", l, c.stream, [&] {
-                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, 0);
+                     launch_pdl(hfn, hgrid, kThreads, 0, c.stream, ws, p, slot, hgroup);
                  })))
                 return rc;
             if ((rc = launch("classify", l, c.stream, [&] {

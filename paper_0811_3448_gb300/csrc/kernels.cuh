@@ -520,9 +520,11 @@ static __global__ void k_prep(Ws ws, int slot) {
 // ---------------------------------------------------------------------------
 // hist: per bucket of the level, counts of the digit at the bucket's bit
 // position and the AND / OR of its encoded keys.  Persistent CTAs take groups
-// of kHistGroup consecutive tiles by ticket, count into per-warp shared
-// histograms, and flush to the bucket (global atomics) only when the bucket
-// changes or the group ends.
+// of `group` (1 .. kHistGroup) consecutive tiles by ticket, count into
+// per-warp shared histograms, and flush to the bucket (global atomics) only
+// when the bucket changes or the group ends.  Large calls take groups of
+// kHistGroup (fewer flushes); small ones smaller groups, so that their few
+// tiles spread over more CTAs (a small sort waits on its slowest CTA).
 // ---------------------------------------------------------------------------
 constexpr int kHistGroup = 8;
 
@@ -552,7 +554,7 @@ __device__ __forceinline__ typename KeyTraits<KB>::Raw shfl_down_raw(typename Ke
 
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
 template <int KB, bool IDENT>
-__global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int buf_unused) {
+__global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int group) {
     pdl_entry();
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
@@ -630,9 +632,9 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
         __syncthreads();
         const uint32_t g = sticket;
         __syncthreads();
-        const uint32_t t0 = g * kHistGroup;
+        const uint32_t t0 = g * (uint32_t)group;
         if (t0 >= nt) break;
-        const uint32_t t1 = min(t0 + kHistGroup, nt);
+        const uint32_t t1 = min(t0 + (uint32_t)group, nt);
         for (uint32_t t = t0; t < t1; t++) {
             const uint32_t b = ws.tilemap[t];
             const Bucket bk = list[b];
@@ -753,6 +755,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     __shared__ unsigned long long scopy_acc;
     __shared__ uint32_t sjob_base;
     __shared__ unsigned long long scopy_base;
+    __shared__ uint32_t sclass[kMaxClasses];  // this parent's jobs per finisher class
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nb = (uint32_t)alloc;
@@ -886,12 +889,11 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
             snjobs = 0;
             scopy_acc = 0ull;
         }
+        if (tid < kMaxClasses) sclass[tid] = 0;
         __syncthreads();
-        if ((tid & 31) == 0) {
+        {
             const uint32_t C = (uint32_t)p.cutoff;
             const uint32_t own = C / 8;       // a child this large is a job of its own
-            long long run_begin = -1;
-            uint32_t run_len = 0, run_children = 0;
             auto emit = [&](long long begin, uint32_t len, uint32_t children) {
                 if (len == 0) return;
                 int jpos = terminal ? W : (children == 1 ? cpos : bk.pos);
@@ -907,52 +909,67 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                 if (slot < (uint32_t)kRadix) sjobs[slot] = j;
                 else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
             };
-            const int d0 = (tid >> 5) * 32;
-            for (int d = d0; d < d0 + 32; d++) {
-                const uint32_t c = scount[d];
-                if (c == 0) continue;
-                const long long cb = bk.begin + sexcl[d];
-                const bool big = !terminal && c > C;
-                if (terminal && c > C) {
-                    // finished and large: copy job if it sits in the workspace
-                    emit(run_begin, run_len, run_children);
-                    run_begin = -1; run_len = 0; run_children = 0;
-                    if (cbuf == 1) {
-                        const uint32_t tiles = (c + T - 1) / T;
-                        const unsigned long long got =
-                            atomicAdd(&scopy_acc, ((unsigned long long)tiles << 32) | 1ull);
-                        const uint32_t slot = (uint32_t)got;
-                        CopyJob cj;
-                        cj.begin = cb;
-                        cj.len = c;
-                        cj.tile_start = (uint32_t)(got >> 32);
-                        if (slot < (uint32_t)kRadix) scopies[slot] = cj;
-                        else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+            // finished and large: copy job if it sits in the workspace
+            auto copy_child = [&](long long cb, uint32_t c) {
+                if (cbuf != 1) return;
+                const uint32_t tiles = (c + T - 1) / T;
+                const unsigned long long got =
+                    atomicAdd(&scopy_acc, ((unsigned long long)tiles << 32) | 1ull);
+                const uint32_t slot = (uint32_t)got;
+                CopyJob cj;
+                cj.begin = cb;
+                cj.len = c;
+                cj.tile_start = (uint32_t)(got >> 32);
+                if (slot < (uint32_t)kRadix) scopies[slot] = cj;
+                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+            };
+            const int d0 = (tid >> 5) * 32, lane = tid & 31;
+            const uint32_t cl = scount[d0 + lane];
+            const bool big_l = !terminal && cl > C, term_l = terminal && cl > C;
+            // a child that would join a merged run (0 < c < own, not large)
+            const bool small_l = cl > 0 && !big_l && !term_l && cl < own;
+            if (!__any_sync(0xffffffffu, small_l)) {
+                // no run to merge in this group: every lane handles its digit
+                const long long cb = bk.begin + sexcl[d0 + lane];
+                if (term_l) copy_child(cb, cl);
+                else if (!big_l && cl > 0) emit(cb, cl, 1);
+            } else if (lane == 0) {
+                long long run_begin = -1;
+                uint32_t run_len = 0, run_children = 0;
+                for (int d = d0; d < d0 + 32; d++) {
+                    const uint32_t c = scount[d];
+                    if (c == 0) continue;
+                    const long long cb = bk.begin + sexcl[d];
+                    const bool big = !terminal && c > C;
+                    if (terminal && c > C) {
+                        emit(run_begin, run_len, run_children);
+                        run_begin = -1; run_len = 0; run_children = 0;
+                        copy_child(cb, c);
+                        continue;
                     }
-                    continue;
+                    if (big) {
+                        emit(run_begin, run_len, run_children);
+                        run_begin = -1; run_len = 0; run_children = 0;
+                        continue;
+                    }
+                    if (c >= own) {
+                        emit(run_begin, run_len, run_children);
+                        run_begin = -1; run_len = 0; run_children = 0;
+                        emit(cb, c, 1);
+                        continue;
+                    }
+                    if (run_begin >= 0 && run_len + c <= C) {
+                        run_len += c;
+                        run_children += 1;
+                    } else {
+                        emit(run_begin, run_len, run_children);
+                        run_begin = cb;
+                        run_len = c;
+                        run_children = 1;
+                    }
                 }
-                if (big) {
-                    emit(run_begin, run_len, run_children);
-                    run_begin = -1; run_len = 0; run_children = 0;
-                    continue;
-                }
-                if (c >= own) {
-                    emit(run_begin, run_len, run_children);
-                    run_begin = -1; run_len = 0; run_children = 0;
-                    emit(cb, c, 1);
-                    continue;
-                }
-                if (run_begin >= 0 && run_len + c <= C) {
-                    run_len += c;
-                    run_children += 1;
-                } else {
-                    emit(run_begin, run_len, run_children);
-                    run_begin = cb;
-                    run_len = c;
-                    run_children = 1;
-                }
+                emit(run_begin, run_len, run_children);
             }
-            emit(run_begin, run_len, run_children);
         }
         __syncthreads();
         if (tid == 0) {
@@ -969,7 +986,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
             const uint32_t ji = sjob_base + tid;
             if (ji < ws.jcap) {
                 ws.jobs[ji] = j;
-                atomicAdd(&ws.ctr->class_count[finish_class<KB>(j.len)], 1u);
+                atomicAdd(&sclass[finish_class<KB>(j.len)], 1u);
             } else {
                 set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
             }
@@ -982,6 +999,9 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
             else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
         }
         __syncthreads();
+        // one global atomic per class instead of one per job (the same thread
+        // clears its entry before the next parent's jobs are counted)
+        if (tid < kMaxClasses && sclass[tid]) atomicAdd(&ws.ctr->class_count[tid], sclass[tid]);
     }
 }
 
