@@ -83,7 +83,9 @@ typedef struct {
                                4 .. 8 (the in-place mode takes 0 or 1) */
     int small_cutoff;       /* C: buckets of <= C keys are finished in shared memory;
                                2048 .. the finisher capacity: 8192 / 4096 / 2048
-                               keys for 4 / 8 / 16-byte keys (0: the capacity) */
+                               keys for 4 / 8 / 16-byte keys (0: the capacity, or
+                               for 4-byte keys in calls of at most 2^21 keys 4096,
+                               6144 or 3072 by the call's size) */
     int ctas_per_sm;        /* persistent CTAs per SM for the partition kernels (0 = max) */
     int64_t lookback_timeout_ns; /* limit on one look-back wait (0 = 1 s) */
     int debug_skip_publish_tile; /* TEST HOOK: if > 0, tile (value-1) of the first partition
