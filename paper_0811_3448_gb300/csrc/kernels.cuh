@@ -1495,6 +1495,55 @@ __device__ __forceinline__ bool finish_fast(FinishSmem<KB, VB, IU> &s, const Ws 
         // P fits the key's width when the position needs at most f + 12 bits.
         const int sft = f + kFinishBits;
         const int nidx = 32 - __clz((uint32_t)(len - 1) | 1u);
+        if (sft < W && nidx <= f) {
+            // Jobs below the first levels (f >= the position's bits): the word
+            // P = (key bits below f) << nidx | input position holds the whole
+            // key below its common prefix, so it orders a run and also carries
+            // the run's 12-bit digit (bits nidx + W - sft up): no digit array
+            // to write at placement and read at ranking.
+            Bits *sp = reinterpret_cast<Bits *>(s.keys);
+            const int up = f - nidx;
+#pragma unroll
+            for (int k = 0; k < IU; k++) {
+                const int i = k * kThreads + tid;
+                if (i < len) {
+                    const uint32_t d = dr[k] >> 16;
+                    const uint32_t at = (fs.cs[d] & 0xffffu) + (dr[k] & 0xffffu);
+                    if (at < (uint32_t)len) sp[at] = ((e[k] << f) >> up) | (Bits)i;
+                    else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                }
+            }
+            __syncthreads();
+            const Bits pre = a & (KT::ones() << (W - f));     // f >= nidx >= 1
+            const Bits imask = ((Bits)1 << nidx) - 1;
+            const int dsh = nidx + W - sft;
+#pragma unroll 2
+            for (int k = 0; k < IU; k++) {
+                const int x = k * kThreads + tid;
+                if (x < len) {
+                    const Bits px = sp[x];
+                    const uint32_t d = (uint32_t)(px >> dsh) & (uint32_t)(kFinishBins - 1);
+                    const uint32_t bc = fs.cs[d];
+                    const int b0 = (int)(bc & 0xffffu), m = (int)(bc >> 16);
+                    int rank = 0;
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const Bits py = sp[b0 + t];        // b0 + 3 <= len + 2: in the buffer
+                        rank += (t < m && py < px) ? 1 : 0;
+                    }
+                    for (int y = b0 + 4; y < b0 + m; y++) rank += sp[y] < px ? 1 : 0;
+                    uint32_t ix = (uint32_t)(px & imask);
+                    if (ix >= (uint32_t)len) {
+                        set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                        ix = 0;
+                    }
+                    const int at = min(b0 + rank, len - 1);
+                    dst[at] = dec(pre | (px >> nidx));
+                    if (VB) vdst[at] = svals[vs + ix];
+                }
+            }
+            return true;
+        }
         if (sft >= W || nidx <= sft) {
             Bits *sp = reinterpret_cast<Bits *>(s.keys);
             uint16_t *sd = s.perm;
