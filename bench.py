@@ -63,6 +63,9 @@ def parse_args():
     ap.add_argument("--seg-len", type=int, default=0,
                     help="segments: equal segments of this many keys instead of the "
                          "20,000 log-uniform ones")
+    ap.add_argument("--seg-prefix-bits", type=int, default=0,
+                    help="segments: the keys of a segment share their top B bits, like the "
+                         "jobs a full sort hands its finisher after B / 8 levels")
     ap.add_argument("--no-plain", action="store_true",
                     help="segments: skip the one-call-per-segment comparison")
     ap.add_argument("--no-autotune", action="store_true",
@@ -629,6 +632,13 @@ def run_segments(args):
     off_h = inputs.offsets_from_sizes(sizes)
     n = int(off_h[-1])
     keys_h = inputs.uniform_keys(n, np.uint32, inputs.rng(4, 1))
+    b = args.seg_prefix_bits
+    if 0 < b < 32:
+        # every segment's keys share a top-b-bit prefix of their own
+        seg_of = np.repeat(np.arange(len(sizes), dtype=np.uint64), sizes)
+        prefix = (seg_of * np.uint64(0x9E3779B1)) & np.uint64((1 << b) - 1)
+        keys_h = ((prefix << np.uint64(32 - b)) |
+                  (keys_h.astype(np.uint64) >> np.uint64(b))).astype(np.uint32)
     vals_h = inputs.segment_index_payload(off_h)
     dev = torch.device("cuda", local)
     off = torch.from_numpy(off_h).to(dev)
@@ -696,7 +706,9 @@ def run_segments(args):
            "data": "synthetic",
            "config": {"workload": (f"{segs} segments of {args.seg_len} keys" if args.seg_len > 0 else
                                    "20,000 segments, log-uniform sizes in [1, 2^20] rescaled to")
-                                  + f" {n} uint32 keys + uint32 payload, one CUDA-graph launch",
+                                  + f" {n} uint32 keys + uint32 payload, one CUDA-graph launch"
+                                  + (f", keys of a segment sharing their top {args.seg_prefix_bits} bits"
+                                     if 0 < args.seg_prefix_bits < 32 else ""),
                       "segments": segs, "n": n, "parallelism": f"replicas x{world}",
                       "l2": "1 GiB keys + 1 GiB payloads restored before every replay"},
            "autotuned": {"tile_keys": cfg.tile_keys, "bits_per_pass": cfg.bits_per_pass,
