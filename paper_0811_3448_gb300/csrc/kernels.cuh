@@ -635,19 +635,25 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
         const uint32_t t0 = g * (uint32_t)group;
         if (t0 >= nt) break;
         const uint32_t t1 = min(t0 + (uint32_t)group, nt);
-        for (uint32_t t = t0; t < t1; t++) {
+        for (uint32_t t = t0; t < t1;) {
             const uint32_t b = ws.tilemap[t];
             const Bucket bk = list[b];
+            // the group's consecutive tiles of this bucket are one contiguous
+            // range of keys, read in one loop (no partial round per tile)
+            const uint32_t tcur = t;
+            const uint32_t tend =
+                min(t1, bk.tile_start + (uint32_t)(((long long)bk.len + T - 1) / T));
+            t = tend > tcur ? tend : tcur + 1;
             if (bk.flags & (kHasHist | kSkip)) continue;
             if (b != cur_b) {
                 if (cur_b != 0xffffffffu) flush();
                 cur_b = b;
             }
-            const long long tb = bk.begin + (long long)(t - bk.tile_start) * T;
-            const int tlen = (int)min((long long)T, bk.begin + (long long)bk.len - tb);
+            const long long tb = bk.begin + (long long)(tcur - bk.tile_start) * T;
+            const int tlen = (int)min((long long)(t - tcur) * T, bk.begin + (long long)bk.len - tb);
             const Raw *src = reinterpret_cast<const Raw *>(bk.buf ? ws.alt_keys : p.keys) + tb;
             // 16-byte chunks from the boundary at or below src (every chunk holds
-            // at least one key of the tile); keys outside the tile are skipped
+            // at least one key of the range); keys outside the range are skipped
             const uintptr_t a1 = reinterpret_cast<uintptr_t>(src);
             const uintptr_t a0 = a1 & ~(uintptr_t)15;
             const int shift = (int)((a1 - a0) / KB);
