@@ -56,8 +56,10 @@ static_assert(sizeof(Job) == 16, "Job layout");
 // A finished bucket larger than the finisher cutoff that must still be moved:
 // copied back from the workspace arrays to the caller's, or (kCopyReverse)
 // reversed -- strictly decreasing keys -- into the caller's arrays, in place
-// when it already sits there (kCopyInPlace).  The flags ride in the top bits
-// of `begin` (key indices stay below 2^61).
+// when it already sits there (kCopyInPlace).  A bucket whose keys are all
+// equal (kCopyFill) gets its one key written, not read, and only its payloads
+// copied.  The flags ride in the top bits of `begin` (key indices stay below
+// 2^60).
 struct CopyJob {
     long long begin;
     uint32_t len;
@@ -66,7 +68,8 @@ struct CopyJob {
 static_assert(sizeof(CopyJob) == 16, "CopyJob layout");
 constexpr long long kCopyReverse = 1LL << 62;
 constexpr long long kCopyInPlace = 1LL << 61;
-constexpr long long kCopyBeginMask = (1LL << 61) - 1;
+constexpr long long kCopyFill = 1LL << 60;
+constexpr long long kCopyBeginMask = (1LL << 60) - 1;
 
 // Order flags of a bucket's adjacent key pairs (encoded keys).
 constexpr uint32_t kHasDescent = 1;      // some key[i] > key[i+1]

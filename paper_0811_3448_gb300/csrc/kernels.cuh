@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                             set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
                         } else {
                             CopyJob cj;
-                            cj.begin = bk.begin;
+                            cj.begin = bk.begin | kCopyFill;       // all keys equal
                             cj.len = bk.len;
                             cj.tile_start = (uint32_t)(got >> 32);
                             ws.copies[ci] = cj;
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                     atomicAdd(&scopy_acc, ((unsigned long long)tiles << 32) | 1ull);
                 const uint32_t slot = (uint32_t)got;
                 CopyJob cj;
-                cj.begin = cb;
+                cj.begin = cb | kCopyFill;      // every key bit consumed: all keys equal
                 cj.len = c;
                 cj.tile_start = (uint32_t)(got >> 32);
                 if (slot < (uint32_t)kRadix) scopies[slot] = cj;
@@ -1320,7 +1320,7 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
 // ---------------------------------------------------------------------------
 constexpr int kFinishBits = 12;
 constexpr int kFinishBins = 1 << kFinishBits;
-constexpr int kFinishRun = 32;
+constexpr int kFinishRun = 128;
 
 // Split counters: 16-bit counts, two bins per word, in the first half of cs;
 // after the scan cs[d] = start of bin d | count of bin d << 16 (counts and
@@ -1910,6 +1910,27 @@ __device__ __forceinline__ void copy_range(E *dst, const E *src, long long count
         dst[i] = src[i];
 }
 
+// Writes `count` copies of v by the whole CTA: 16-byte vectors of v from the
+// first 16-byte boundary (after a scalar head), scalar for the tail.
+template <typename E>
+__device__ __forceinline__ void fill_range(E *dst, const E &v, long long count) {
+    static_assert(16 % sizeof(E) == 0, "element size divides 16");
+    constexpr int PER = 16 / (int)sizeof(E);
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst);
+    const long long head = min(count, (long long)(((16 - (d & 15)) & 15) / sizeof(E)));
+    for (long long i = threadIdx.x; i < head; i += kThreads) dst[i] = v;
+    union {
+        E e[PER];
+        uint4 u;
+    } w;
+#pragma unroll
+    for (int q = 0; q < PER; q++) w.e[q] = v;
+    const long long nvec = (count - head) / PER;
+    uint4 *dv = reinterpret_cast<uint4 *>(dst + head);
+    for (long long i = threadIdx.x; i < nvec; i += kThreads) dv[i] = w.u;
+    for (long long i = head + nvec * PER + threadIdx.x; i < count; i += kThreads) dst[i] = v;
+}
+
 // T: the call's tile (copy jobs are cut into tiles of the partition's size).
 template <int KB, int VB>
 __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, int T, void *keys0, void *keys1,
@@ -1940,11 +1961,15 @@ __global__ void __launch_bounds__(kThreads) k_copy(Ws ws, int T, void *keys0, vo
         const long long j1 = min(j0 + T, len);
         const bool rev = (cj.begin & kCopyReverse) != 0;
         const bool inplace = (cj.begin & kCopyInPlace) != 0;
+        const bool fill = (cj.begin & kCopyFill) != 0;
         Raw *dst = reinterpret_cast<Raw *>(keys0) + cb;
         V *vdst = VB ? reinterpret_cast<V *>(vals0) + cb : nullptr;
         if (!rev) {
             // from the workspace arrays, straight
-            copy_range<Raw>(dst + j0, reinterpret_cast<const Raw *>(keys1) + cb + j0, j1 - j0);
+            if (fill)      // all keys equal: the first one, written over the range
+                fill_range<Raw>(dst + j0, reinterpret_cast<const Raw *>(keys1)[cb], j1 - j0);
+            else
+                copy_range<Raw>(dst + j0, reinterpret_cast<const Raw *>(keys1) + cb + j0, j1 - j0);
             if (VB) copy_range<V>(vdst + j0, reinterpret_cast<const V *>(vals1) + cb + j0, j1 - j0);
         } else if (!inplace) {
             // from the workspace arrays, reversed
