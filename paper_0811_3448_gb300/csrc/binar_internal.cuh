@@ -77,6 +77,14 @@ constexpr uint32_t kHasNonDescent = 2;   // some key[i] <= key[i+1]
 
 constexpr int kMaxClasses = 8;          // finisher size classes
 
+// Job indices are kept per finisher size class, each class in a region of
+// its own: class 0 (jobs of up to 1024 keys) may hold every job (jcap), and
+// every later class only jobs of more than 1024 keys -- disjoint key ranges,
+// so at most n / 1025 + 1 of them.  Region c starts at job_region(c, ...).
+__host__ __device__ inline unsigned long long job_region(int c, long long n, unsigned long long jcap) {
+    return c == 0 ? 0ull : jcap + (unsigned long long)(c - 1) * (unsigned long long)(n / 1025 + 1);
+}
+
 struct Counters {
     uint32_t status;                  // first device error (binar_status), 0 = OK
     uint32_t njobs;                   // finisher jobs
@@ -88,7 +96,7 @@ struct Counters {
     uint32_t ticket_fin2;
     uint32_t pad[5];
     uint32_t class_count[kMaxClasses];   // finisher jobs per size class
-    uint32_t class_cursor[kMaxClasses];  // binning cursors
+    uint32_t class_unused[kMaxClasses];
     uint32_t class_ticket[kMaxClasses];  // per-class work tickets
 };
 static_assert(sizeof(Counters) == 176, "Counters layout");

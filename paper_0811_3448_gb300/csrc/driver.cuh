@@ -44,8 +44,8 @@ int launch_partition(const Call &c, const Ws &ws, const Params &p, int slot, int
 }
 
 // Sorts of at most this many keys finish every job in one launch, of the
-// smallest class that holds the largest job the call can have, without the
-// binning pass (fewer launches; idle items in smaller jobs cost little at
+// smallest class that holds the largest job the call can have, instead of one
+// launch per class (fewer launches; idle items in smaller jobs cost little at
 // that size).
 constexpr long long kOneFinishLaunchMaxN = 1LL << 21;
 
@@ -181,11 +181,6 @@ int run_inplace(const Call &c) {
                 return rc;
         }
     }
-    if (c.n > kOneFinishLaunchMaxN && (rc = launch("bin_jobs", -1, c.stream, [&] {
-             launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
-                        c.stream, ws);
-         })))
-        return rc;
     if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k0, v0, v0,
                                              std::make_integer_sequence<int, FinishClasses<KB>::kCount>{})))
         return rc;
@@ -309,11 +304,6 @@ int run_call_vb(const Call &c) {
         }
     }
     {
-        if (c.n > kOneFinishLaunchMaxN && (rc = launch("bin_jobs", -1, c.stream, [&] {
-                 launch_pdl(k_bin_jobs<KB>, cap_grid(small_grid, c.n / (2LL * kThreads) + 1), kThreads, 0,
-                            c.stream, ws);
-             })))
-            return rc;
         if ((rc = launch_finish_classes<KB, VB>(c, ws, p, k0, k1, v0, v1,
                                                  std::make_integer_sequence<int, FinishClasses<KB>::kCount>{})))
             return rc;

@@ -369,6 +369,10 @@ template <> struct FinishClasses<16> {
     __host__ __device__ static constexpr int iu(int c) { return c == 0 ? 4 : 8; }
 };
 
+static_assert(kThreads * FinishClasses<4>::iu(0) == 1024 && kThreads * FinishClasses<8>::iu(0) == 1024 &&
+                  kThreads * FinishClasses<16>::iu(0) == 1024,
+              "job_region: every class above 0 holds jobs of more than 1024 keys");
+
 template <int KB>
 __device__ __forceinline__ int finish_class(uint32_t len) {
     int c = 0;
@@ -376,16 +380,20 @@ __device__ __forceinline__ int finish_class(uint32_t len) {
     return c;
 }
 
-// Appends a finisher job and counts it in its size class.
+// Appends a finisher job, counts it in its size class and lists its index in
+// the class's region of jobidx (n: the call's keys, which bound the regions).
 template <int KB>
-__device__ __forceinline__ void push_job(const Ws &ws, const Job &j) {
+__device__ __forceinline__ void push_job(const Ws &ws, const Job &j, long long n) {
     const uint32_t ji = atomicAdd(&ws.ctr->njobs, 1u);
     if (ji >= ws.jcap) {
         set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
         return;
     }
     ws.jobs[ji] = j;
-    atomicAdd(&ws.ctr->class_count[finish_class<KB>(j.len)], 1u);
+    const int c = finish_class<KB>(j.len);
+    const unsigned long long at = job_region(c, n, ws.jcap) + atomicAdd(&ws.ctr->class_count[c], 1u);
+    if (at < job_region(c + 1, n, ws.jcap)) ws.jobidx[at] = ji;
+    else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,7 +426,7 @@ __global__ void k_init(Ws ws, long long n, int cutoff, int pos0, uint32_t tiles0
         j.pos = (uint16_t)pos0;
         j.buf = 0;
         j.pad = 0;
-        push_job<KB>(ws, j);
+        push_job<KB>(ws, j, n);
     }
 }
 
@@ -470,7 +478,7 @@ __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_s
             j.pos = 0;
             j.buf = 0;
             j.pad = 0;
-            push_job<KB>(ws, j);
+            push_job<KB>(ws, j, n);
         }
     }
 }
@@ -762,6 +770,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
     __shared__ uint32_t sjob_base;
     __shared__ unsigned long long scopy_base;
     __shared__ uint32_t sclass[kMaxClasses];  // this parent's jobs per finisher class
+    __shared__ uint32_t sclass_base[kMaxClasses];   // and their first slot in the class region
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nb = (uint32_t)alloc;
@@ -987,12 +996,16 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
                                   : 0ull;
         }
         __syncthreads();
+        int jcls = 0;
+        uint32_t jslot = 0;
+        const uint32_t ji = sjob_base + tid;
+        const bool jvalid = tid < (int)snjobs && ji < ws.jcap;
         if (tid < (int)snjobs) {
             const Job j = sjobs[tid];
-            const uint32_t ji = sjob_base + tid;
-            if (ji < ws.jcap) {
+            if (jvalid) {
                 ws.jobs[ji] = j;
-                atomicAdd(&sclass[finish_class<KB>(j.len)], 1u);
+                jcls = finish_class<KB>(j.len);
+                jslot = atomicAdd(&sclass[jcls], 1u);
             } else {
                 set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
             }
@@ -1005,9 +1018,17 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
             else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
         }
         __syncthreads();
-        // one global atomic per class instead of one per job (the same thread
-        // clears its entry before the next parent's jobs are counted)
-        if (tid < kMaxClasses && sclass[tid]) atomicAdd(&ws.ctr->class_count[tid], sclass[tid]);
+        // one global atomic per class instead of one per job: this parent's
+        // first slot in each class region (the same thread clears its entry
+        // before the next parent's jobs are counted)
+        if (tid < kMaxClasses && sclass[tid])
+            sclass_base[tid] = atomicAdd(&ws.ctr->class_count[tid], sclass[tid]);
+        __syncthreads();
+        if (jvalid) {
+            const unsigned long long at = job_region(jcls, p.n, ws.jcap) + sclass_base[jcls] + jslot;
+            if (at < job_region(jcls + 1, p.n, ws.jcap)) ws.jobidx[at] = ji;
+            else set_status(ws.ctr, BINAR_ERR_QUEUE_OVERFLOW);
+        }
     }
 }
 
@@ -1348,27 +1369,6 @@ struct FinishSmem {
     uint16_t perm[T];
 };
 
-// bin_jobs: the job indices, grouped by size class (classes in order).
-template <int KB>
-__global__ void k_bin_jobs(Ws ws) {
-    pdl_entry();
-    if (has_error(ws.ctr)) return;
-    constexpr int NC = FinishClasses<KB>::kCount;
-    uint32_t base[NC];
-    uint32_t run = 0;
-#pragma unroll
-    for (int c = 0; c < NC; c++) {
-        base[c] = run;
-        run += ws.ctr->class_count[c];
-    }
-    const uint32_t nj = min(ws.ctr->njobs, ws.jcap);
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nj; j += gridDim.x * blockDim.x) {
-        const int c = finish_class<KB>(ws.jobs[j].len);
-        const uint32_t at = base[c] + atomicAdd(&ws.ctr->class_cursor[c], 1u);
-        if (at < ws.jcap) ws.jobidx[at] = j;
-    }
-}
-
 // AND / OR of the job's encoded keys across the CTA (k-wide keys reduce only
 // their live 32-bit words).
 template <int KB>
@@ -1679,12 +1679,11 @@ __global__ void __launch_bounds__(kThreads, (VB == 0 && FinishClasses<KB>::iu(CL
     const Decoder<KB> dec(IDENT ? (int)BINAR_MAP_UNSIGNED : p.map);
     // all_jobs: this launch (of the smallest class that holds the call's
     // largest possible job) takes every job of the call straight from the
-    // job list, unbinned (small sorts: one launch instead of the binning pass
-    // and one per class)
-    uint32_t base = 0;
-    for (int c = 0; c < CLS; c++) base += ws.ctr->class_count[c];
+    // job list (small sorts: one launch instead of one per class); otherwise
+    // the jobs of this class, listed in its region of jobidx
+    const unsigned long long base = job_region(CLS, p.n, ws.jcap);
     const uint32_t count = all_jobs ? min(ws.ctr->njobs, ws.jcap) : ws.ctr->class_count[CLS];
-    if (count == 0 || (!all_jobs && base + count > ws.jcap)) return;
+    if (count == 0 || (!all_jobs && base + count > job_region(CLS + 1, p.n, ws.jcap))) return;
     const uint32_t *mine = all_jobs ? nullptr : ws.jobidx + base;
     const int tid = threadIdx.x;
     uint32_t phase = 0;

@@ -143,7 +143,7 @@ inline Layout make_layout(long long n, long long segs, int kb, int vb) {
     L.tilemap = take((size_t)t * sizeof(uint32_t));
     L.cells = take((size_t)t * kRadix * sizeof(uint32_t));
     L.jobs = take((size_t)j * sizeof(Job));
-    L.jobidx = take((size_t)j * sizeof(uint32_t));
+    L.jobidx = take((size_t)job_region(kMaxClasses, n, (unsigned long long)j) * sizeof(uint32_t));
     L.jobs2 = take((size_t)j * sizeof(Job));
     L.copies = take((size_t)c * sizeof(CopyJob));
     L.total = o;
@@ -194,7 +194,7 @@ inline InplaceLayout make_inplace_layout(long long n, int kb, int cutoff) {
     B.tilemap = take((size_t)t * sizeof(uint32_t));
     B.cells = take(0);
     B.jobs = take((size_t)j * sizeof(Job));
-    B.jobidx = take((size_t)j * sizeof(uint32_t));
+    B.jobidx = take((size_t)job_region(kMaxClasses, n, (unsigned long long)j) * sizeof(uint32_t));
     B.jobs2 = take((size_t)j * sizeof(Job));
     B.copies = take((size_t)c * sizeof(CopyJob));
     L.mask = take((size_t)t * (T / 32) * 4);
