@@ -76,6 +76,7 @@ constexpr uint32_t kHasDescent = 1;      // some key[i] > key[i+1]
 constexpr uint32_t kHasNonDescent = 2;   // some key[i] <= key[i+1]
 
 constexpr int kMaxClasses = 8;          // finisher size classes
+constexpr int kIpChunk = 1024;          // in-place mode: exchanged pairs per swap work item
 
 // Job indices are kept per finisher size class, each class in a region of
 // its own: class 0 (jobs of up to 1024 keys) may hold every job (jcap), and

@@ -33,7 +33,6 @@ namespace binar {
 
 constexpr int kIpTile = 4096;                 // keys per tile of the in-place passes
 constexpr int kIpWords = kIpTile / 32;        // marker words per tile (four per lane of a warp)
-constexpr int kIpChunk = 1024;                // exchanged pairs per swap work item
 constexpr int kIpScanItems = 8;
 constexpr int kIpScanTile = kThreads * kIpScanItems;   // tiles per scan block
 
@@ -216,13 +215,14 @@ static __global__ void __launch_bounds__(kThreads) k_ip_scan_apply(Ws ws, int sl
 // with a missing or foreign position is reported (BINAR_ERR_DEVICE_BOUNDS)
 // and skipped.  Each thread loads its pairs before storing them.
 template <int KB, int VB>
-__global__ void __launch_bounds__(kThreads) k_ip_swap(Ws ws, Params p, int slot, IpWs ip) {
+__global__ void __launch_bounds__(kThreads, 4) k_ip_swap(Ws ws, Params p, int slot, IpWs ip) {
     pdl_entry();
     using Raw = typename KeyTraits<KB>::Raw;
     using V = typename ValTraits<VB>::T;
     constexpr int PER = kIpChunk / kThreads;              // pairs per thread
-    __shared__ long long pos[2][kIpChunk];
+    __shared__ int pos[2][kIpChunk];       // key positions (n < 2^31)
     __shared__ uint32_t sfirst;
+    __shared__ uint32_t sscan[kWarps];
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = slot ? ws.ctr->alloc[1] : ws.ctr->alloc[0];
     const uint32_t nt = (uint32_t)(alloc >> 32);
@@ -245,42 +245,31 @@ __global__ void __launch_bounds__(kThreads) k_ip_swap(Ws ws, Params p, int slot,
                 sfirst = f < nt ? f : 0u;
             }
             __syncthreads();
-            for (uint32_t base = sfirst; base < nt; base += kWarps) {
-                if (ip.pre[2 * (size_t)base + side] >= hi) break;      // uniform
-                const uint32_t t = base + w;
-                if (t < nt) {
-                    const unsigned long long r0 = ip.pre[2 * (size_t)t + side];
-                    uint32_t bits[4] = {0u, 0u, 0u, 0u};
-                    long long wb = 0;
-                    if (r0 < hi) {       // a skipped bucket's tiles have no marker bits
-                        const long long tb = ip.tinfo[2 * (size_t)t], mid = ip.tinfo[2 * (size_t)t + 1];
-                        const uint4 mw = reinterpret_cast<const uint4 *>(ip.mask + (size_t)t * kIpWords)[lane];
-                        bits[0] = mw.x; bits[1] = mw.y; bits[2] = mw.z; bits[3] = mw.w;
-                        wb = tb + (long long)lane * 128;
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {     // keep the bits of this side of mid
-                            const long long cut = mid - (wb + 32 * k);
-                            const uint32_t low = cut >= 32 ? 0xffffffffu : (cut <= 0 ? 0u : ((1u << cut) - 1u));
-                            bits[k] &= side == 0 ? low : ~low;
-                        }
-                    }
-                    const uint32_t cntb = __popc(bits[0]) + __popc(bits[1]) + __popc(bits[2]) + __popc(bits[3]);
-                    uint32_t incl = cntb;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    unsigned long long r = r0 + incl - cntb;
-#pragma unroll
-                    for (int k = 0; k < 4; k++) {
-                        uint32_t x = bits[k];
-                        while (x) {
-                            const int j = __ffs(x) - 1;
-                            x &= x - 1;
-                            if (r >= lo && r < hi) pos[side][r - lo] = wb + 32 * k + j;
-                            r++;
-                        }
+            // the tiles holding ranks [lo, hi) on this side, one at a time,
+            // their 4096 marker bits spread over the CTA (16 per thread): a
+            // block scan of the popcounts gives every bit its rank, and each
+            // thread records the positions of its bits whose ranks are the
+            // chunk's.  Tiles without marked keys on this side are passed over.
+            for (uint32_t t = sfirst; t < nt; t++) {
+                const unsigned long long r0 = ip.pre[2 * (size_t)t + side];    // uniform
+                if (r0 >= hi) break;
+                if (ip.cnt[2 * (size_t)t + side] == 0) continue;                // uniform
+                const long long tb = ip.tinfo[2 * (size_t)t], mid = ip.tinfo[2 * (size_t)t + 1];
+                const uint32_t word = ip.mask[(size_t)t * kIpWords + (tid >> 1)];
+                uint32_t bits = (word >> ((tid & 1) * 16)) & 0xffffu;
+                const long long wb = tb + (long long)tid * 16;
+                const long long cut = mid - wb;             // bits below cut lie left of mid
+                const uint32_t low = cut >= 16 ? 0xffffu : (cut <= 0 ? 0u : ((1u << cut) - 1u));
+                bits &= side == 0 ? low : (~low & 0xffffu);
+                uint32_t total;
+                const uint32_t nb = (uint32_t)__popc(bits);
+                unsigned long long r = r0 + block_exclusive_scan(nb, sscan, &total);
+                if (r < hi && r + nb > lo) {
+                    while (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        if (r >= lo && r < hi) pos[side][r - lo] = (int)(wb + j);
+                        r++;
                     }
                 }
             }

@@ -202,7 +202,7 @@ inline InplaceLayout make_inplace_layout(long long n, int kb, int cutoff) {
     L.pre = take((size_t)t * 8);
     L.bsum = take((size_t)(t / (256 * 8) + 2) * 8);
     L.total = take(16);
-    L.chunks = n / (2 * 1024) + 2;                // kIpChunk ranks per chunk; misplaced <= n / 2
+    L.chunks = n / (2 * kIpChunk) + 2;            // kIpChunk ranks per chunk; misplaced <= n / 2
     L.first = take((size_t)L.chunks * 2 * 4);
     L.tinfo = take((size_t)t * 16);
     B.total = o;
