@@ -210,10 +210,25 @@ def cpu_baseline(n_sample: int, dist: str, kdt=np.uint32):
     t0 = time.perf_counter()
     oracle.binar_sort_parallel(k, vals, log2_groups=log2g)
     dt = time.perf_counter() - t0
-    return {"value": n_sample / dt / 1e9, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
-            "sample": f"{n_sample} {np.dtype(kdt).name} keys + uint32 payload ({dist}), parallel binar sort "
-                      f"(leading-bit split, one thread per group), {dt:.2f} s wall",
-            "validated": host_sorted_pairs(keys, k, vals)}
+    out = {"value": n_sample / dt / 1e9, "unit": UNIT, "cores": 1 << log2g, "kind": "oracle",
+           "sample": f"{n_sample} {np.dtype(kdt).name} keys + uint32 payload ({dist}), parallel binar sort "
+                     f"(leading-bit split, one thread per group), {dt:.2f} s wall",
+           "validated": host_sorted_pairs(keys, k, vals)}
+    # context, one host thread on a smaller sample: the paper's sequential
+    # binar sort (keys alone, in place) and the library sort of numpy
+    m = max(1, n_sample // 8)
+    k1 = keys[:m].copy()
+    t0 = time.perf_counter()
+    oracle.binar_sort(k1)
+    t1 = time.perf_counter()
+    k2 = np.sort(keys[:m], kind="stable")
+    t2 = time.perf_counter()
+    out["single_thread"] = {
+        "sample": f"{m} {np.dtype(kdt).name} keys ({dist}), keys alone",
+        "binar_sort_GKeys_per_s": m / (t1 - t0) / 1e9,
+        "numpy_sort_GKeys_per_s": m / (t2 - t1) / 1e9,
+        "validated": bool(np.array_equal(k1, k2))}
+    return out
 
 
 def host_sorted_pairs(orig: np.ndarray, keys: np.ndarray, vals: np.ndarray) -> bool:
