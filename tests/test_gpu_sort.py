@@ -160,3 +160,29 @@ def test_repeated_calls_reuse_workspace():
     ek, ev = expect_pairs(keys, vals)
     assert same_bits(to_host(tk), ek) and same_bits(to_host(tv), ev)
 
+
+
+@pytest.mark.parametrize("kind", ["u32_last_bits", "u64_last_bits", "bytes16_distinct"])
+def test_equal_key_buckets_written_back(kind):
+    """Buckets larger than the cutoff whose keys are all equal and that end up
+    in the workspace are written back from their one key: keys that differ
+    only in their last bits (after a pass-through to the first differing bit
+    the next split consumes the last bits, leaving children of equal keys),
+    and 16-byte keys with a few distinct values (all-equal buckets at the
+    next level).  Payloads: the original index, so stability is checked."""
+    n = 300_001
+    g = np.random.Generator(np.random.PCG64(321))
+    if kind == "u32_last_bits":
+        keys = (np.uint32(0x9ABC0000) + g.choice(np.array([0, 1, 3], np.uint32), size=n)).astype(np.uint32)
+        vals = inputs.index_payload(n)
+    elif kind == "u64_last_bits":
+        keys = (np.uint64(0x123456789AB00000) + g.choice(np.array([0, 2, 5, 7], np.uint64), size=n))
+        vals = np.arange(n, dtype=np.uint64)
+    else:
+        base = g.integers(0, 256, size=(5, 16), dtype=np.uint8)
+        keys = base[g.integers(0, 5, size=n)]
+        vals = np.arange(n, dtype=np.uint64)
+    k, v = gpu_sort_pairs(keys, vals)
+    ek, ev = expect_pairs(keys, vals)
+    assert same_bits(k, ek) and same_bits(v, ev)
+    assert same_bits(gpu_sort_keys(keys), ek)
