@@ -62,8 +62,9 @@ int kernel_ctas_per_sm(const void *fn, size_t smem) {
     std::lock_guard<std::mutex> lk(g_mu);
     for (const auto &e : g_occ)
         if (e.fn == fn && e.dev == dev && e.smem == smem) return e.occ;
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the opt-in covers static plus dynamic shared memory above 48 KB (a
+    // kernel with static arrays can pass the mark with a smaller dynamic part)
+    if (smem > 0) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem) != cudaSuccess)
         occ = 1;

@@ -97,7 +97,8 @@ struct Counters {
     uint32_t ticket_fin2;
     uint32_t pad[5];
     uint32_t class_count[kMaxClasses];   // finisher jobs per size class
-    uint32_t class_unused[kMaxClasses];
+    uint32_t gbar[2];                 // grid barrier of the fused level tail (arrivals, generation)
+    uint32_t unused[kMaxClasses - 2];
     uint32_t class_ticket[kMaxClasses];  // per-class work tickets
 };
 static_assert(sizeof(Counters) == 176, "Counters layout");

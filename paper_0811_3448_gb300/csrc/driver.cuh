@@ -11,6 +11,7 @@
 #include "inplace.cuh"
 #include "kernels.cuh"
 #include "layout.cuh"
+#include "tail.cuh"
 
 namespace binar {
 
@@ -93,6 +94,47 @@ int launch_finish_classes(const Call &c, const Ws &ws, const Params &p, void *k0
     }
     ((rc = rc ? rc : launch_finish_class<KB, VB, CLS>(c, ws, p, k0, k1, v0, v1)), ...);
     return rc;
+}
+
+// Sorts of at most this many keys with the default tile shape run the levels
+// after the first as one cooperative launch (tail.cuh), which ends at the
+// first level without a bucket.
+constexpr long long kTailMaxN = 1LL << 21;
+constexpr int kTailUnavailable = -1;
+
+// Launches levels first .. levels-1 as one cooperative grid; kTailUnavailable
+// (nothing enqueued) when the device cannot make that grid resident, so the
+// caller enqueues the levels one kernel at a time.
+template <int KB, int VB>
+int launch_levels_tail(const Call &c, const Ws &ws, const Params &p, int first, int levels,
+                       long long max_tiles, void *k0, void *k1, void *v0, void *v1) {
+    auto fn = (KB != 16 && c.map == BINAR_MAP_UNSIGNED) ? k_levels_tail<KB, VB, KB != 16>
+                                                        : k_levels_tail<KB, VB, false>;
+    const size_t smem = sizeof(PartitionSmem<KB, VB, (VB > 0), 0>);
+    const int occ = kernel_ctas_per_sm((const void *)fn, smem);
+    const int sms = device_sms();
+    if (occ < 1 || sms < 1) return kTailUnavailable;
+    const int grid = cap_grid((long long)sms * occ, max_tiles);
+    const int hgroup = hist_group(max_tiles, grid);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    bool refused = false;
+    const int rc = launch("levels", first, c.stream, [&] {
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, fn, ws, p, first, levels, hgroup, k0, k1, v0, v1);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+            cudaGetLastError();            // not an error of the call: one kernel per phase instead
+            refused = true;
+        }
+    });
+    return refused ? kTailUnavailable : rc;
 }
 
 // The in-place, unstable mode: one bit per level, keys exchanged across each
@@ -286,6 +328,13 @@ int run_call_vb(const Call &c) {
         const int cgrid = cap_grid(small_grid, max_buckets);
         for (int l = 0; l < L; l++) {
             const int slot = l & 1;
+            if (l == 1 && tv == 0 && c.n <= kTailMaxN) {
+                const int rt = launch_levels_tail<KB, VB>(c, ws, p, 1, L, max_tiles, k0, k1, v0, v1);
+                if (rt != kTailUnavailable) {
+                    if (rt) return rt;
+                    break;
+                }
+            }
             if ((rc = launch("prep", l, c.stream, [&] {
                      launch_pdl(k_prep, pgrid, kThreads, 0, c.stream, ws, slot);
                  })))

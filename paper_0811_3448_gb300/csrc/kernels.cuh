@@ -488,8 +488,7 @@ __global__ void k_seed_segments(Ws ws, const long long *offsets, long long num_s
 // cells, cleared histograms and AND/OR accumulators, reset tickets, and an
 // empty list for the next level.
 // ---------------------------------------------------------------------------
-static __global__ void k_prep(Ws ws, int slot) {
-    pdl_entry();
+__device__ __forceinline__ void prep_body(const Ws &ws, int slot) {
     if (has_error(ws.ctr)) return;
     const unsigned long long alloc = ws.ctr->alloc[slot];
     const uint32_t nb = (uint32_t)alloc, nt = (uint32_t)(alloc >> 32);
@@ -523,6 +522,10 @@ static __global__ void k_prep(Ws ws, int slot) {
         const uint32_t t1 = (b + 1 < nb) ? ws.list[slot][b + 1].tile_start : nt;
         for (uint32_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) ws.tilemap[t] = (uint32_t)b;
     }
+}
+static __global__ void k_prep(Ws ws, int slot) {
+    pdl_entry();
+    prep_body(ws, slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -560,10 +563,18 @@ __device__ __forceinline__ typename KeyTraits<KB>::Raw shfl_down_raw(typename Ke
     }
 }
 
+// A 16-byte load: through the read-only (non-coherent) path when the data
+// cannot change while the kernel runs (NC), else an ordinary load (a kernel
+// that also writes the keys, as the fused tail of small sorts does).
+template <bool NC>
+__device__ __forceinline__ uint4 load16(const uint4 *p) {
+    if constexpr (NC) return __ldg(p);
+    else return *p;
+}
+
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
-template <int KB, bool IDENT>
-__global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int group) {
-    pdl_entry();
+template <int KB, bool IDENT, bool NC>
+__device__ __forceinline__ void hist_body(const Ws &ws, const Params &p, int slot, int group) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using Bits = typename KT::Bits;
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
                 for (int q = 0; q < Q; q++) {
                     const int c = cb + q * kThreads + lane;
                     if (c < nchunk) {
-                        unpack_chunk<KB>(__ldg(c4 + c), r[q]);
+                        unpack_chunk<KB>(load16<NC>(c4 + c), r[q]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < PER; e++) r[q][e] = Raw{};
@@ -710,7 +721,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
                     Raw rafter = shfl_down_raw<KB>(r[q][0]);
                     if (has_after && (lane == 31 || c + 1 >= nchunk)) {   // not in the next lane
                         Raw rn[PER];
-                        unpack_chunk<KB>(__ldg(c4 + c + 1), rn);
+                        unpack_chunk<KB>(load16<NC>(c4 + c + 1), rn);
                         rafter = rn[0];
                     }
                     if (c >= nchunk) continue;
@@ -739,6 +750,11 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
     }
     if (cur_b != 0xffffffffu) flush();
 }
+template <int KB, bool IDENT>
+__global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, int group) {
+    pdl_entry();
+    hist_body<KB, IDENT, true>(ws, p, slot, group);
+}
 
 // ---------------------------------------------------------------------------
 // classify: one CTA per bucket of the level ("Determine Recursive Call on
@@ -753,8 +769,7 @@ __global__ void __launch_bounds__(kThreads) k_hist(Ws ws, Params p, int slot, in
 // finished (all bits consumed; copied back if it sits in the workspace).
 // ---------------------------------------------------------------------------
 template <int KB>
-__global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot, int last_level) {
-    pdl_entry();
+__device__ __forceinline__ void classify_body(const Ws &ws, const Params &p, int slot, int last_level) {
     using KT = KeyTraits<KB>;
     using Bits = typename KT::Bits;
     constexpr int W = KT::kW;
@@ -1031,6 +1046,11 @@ __global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot
         }
     }
 }
+template <int KB>
+__global__ void __launch_bounds__(kThreads) k_classify(Ws ws, Params p, int slot, int last_level) {
+    pdl_entry();
+    classify_body<KB>(ws, p, slot, last_level);
+}
 
 // For binar_partition_pass: exclusive prefix of the single bucket's histogram
 // (kept for the partition kernel) and the caller's group offsets.
@@ -1099,6 +1119,12 @@ __device__ __forceinline__ int chunk_range(const void *src, int len, uintptr_t *
 // tile, which complete on a shared-memory mbarrier; every thread then waits on
 // the barrier's phase.  bulk_begin: the previous use of the destination
 // (ordered by a __syncthreads before the call) comes before the async writes.
+// Invalidates the barrier so that its shared memory can hold other data (the
+// next level of the fused tail); every wait on it has ended (ordered by a
+// __syncthreads before the call).
+__device__ __forceinline__ void mbar_inval(void *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_init(void *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1172,10 +1198,8 @@ __device__ __forceinline__ uint32_t lookback(const Ws &ws, const Params &p, uint
 
 // IDENT: the key map is the identity (BINAR_MAP_UNSIGNED), known at compile time.
 template <int KB, int VB, bool STABLE, bool IDENT, int TV>
-__global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
-    k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
-                void *vals1) {
-    pdl_entry();
+__device__ __forceinline__ void partition_body(const Ws &ws, const Params &p, int slot, int level,
+                                               void *keys0, void *keys1, void *vals0, void *vals1) {
     using KT = KeyTraits<KB>;
     using Raw = typename KT::Raw;
     using V = typename ValTraits<VB>::T;
@@ -1320,6 +1344,13 @@ __global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
         }
         __syncthreads();
     }
+}
+template <int KB, int VB, bool STABLE, bool IDENT, int TV>
+__global__ void __launch_bounds__(kThreads, PartShape<KB, VB, TV>::kMinBlocks)
+    k_partition(Ws ws, Params p, int slot, int level, void *keys0, void *keys1, void *vals0,
+                void *vals1) {
+    pdl_entry();
+    partition_body<KB, VB, STABLE, IDENT, TV>(ws, p, slot, level, keys0, keys1, vals0, vals1);
 }
 
 // ---------------------------------------------------------------------------
