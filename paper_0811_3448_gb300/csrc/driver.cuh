@@ -329,7 +329,7 @@ int run_call_vb(const Call &c) {
         for (int l = 0; l < L; l++) {
             const int slot = l & 1;
             if (l == 1 && tv == 0 && c.n <= kTailMaxN) {
-                const int rt = launch_levels_tail<KB, VB>(c, ws, p, 1, L, max_tiles, k0, k1, v0, v1);
+                const int rt = launch_levels_tail<KB, VB>(c, ws, p, l, L, max_tiles, k0, k1, v0, v1);
                 if (rt != kTailUnavailable) {
                     if (rt) return rt;
                     break;
