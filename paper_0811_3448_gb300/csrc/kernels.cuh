@@ -1205,8 +1205,15 @@ __device__ __forceinline__ void partition_body(const Ws &ws, const Params &p, in
     using V = typename ValTraits<VB>::T;
     constexpr int ITEMS = PartShape<KB, VB, TV>::kItems;
     constexpr int T = PartShape<KB, VB, TV>::kTile;
+    // 4-byte keys with 4-byte payloads are staged as 8-byte records over the
+    // key and payload arrays, which lie back to back
+    constexpr bool KV8 = KB == 4 && VB == 4;
+    using Smem = PartitionSmem<KB, VB, STABLE, TV>;
+    static_assert(!KV8 || offsetof(Smem, vals) == offsetof(Smem, keys) + sizeof(Smem::keys),
+                  "8-byte staging spans the key and payload arrays");
+    static_assert(!KV8 || 8 * T <= sizeof(Smem::keys) + sizeof(Smem::vals), "8-byte staging fits");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &s = *reinterpret_cast<PartitionSmem<KB, VB, STABLE, TV> *>(smem_raw);
+    auto &s = *reinterpret_cast<Smem *>(smem_raw);
     Raw *skeys = reinterpret_cast<Raw *>(s.keys);
     V *svals = reinterpret_cast<V *>(s.vals);
     if (has_error(ws.ctr)) return;
@@ -1298,24 +1305,43 @@ __device__ __forceinline__ void partition_body(const Ws &ws, const Params &p, in
         if (!hooked) st_relaxed(cell, (ti == 0 ? kInclusive : 0u) | (cnt + 1));
 
         // stage the tile in sorted order, in place (its inputs are in registers)
-#pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            const int i = striped(ITEMS, j);
-            if (i < tlen) {
-                const uint32_t r = pk.rank(j);
-                if (r < (uint32_t)tlen) skeys[r] = k[j];
-                else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
-            }
-        }
-        if (VB) {
-            V v[ITEMS];
+        if constexpr (KV8) {
+            // key and payload side by side, one 8-byte store per record into
+            // the bytes of both arrays (every input is in registers after the
+            // barrier)
+            uint32_t v[ITEMS];
 #pragma unroll
             for (int j = 0; j < ITEMS; j++) v[j] = svals[vs + striped(ITEMS, j)];
             __syncthreads();
+            uint2 *skv = reinterpret_cast<uint2 *>(s.keys);
 #pragma unroll
             for (int j = 0; j < ITEMS; j++) {
                 const uint32_t r = pk.rank(j);
-                if (striped(ITEMS, j) < tlen && r < (uint32_t)tlen) svals[r] = v[j];
+                if (striped(ITEMS, j) < tlen) {
+                    if (r < (uint32_t)tlen) skv[r] = make_uint2(k[j], v[j]);
+                    else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                const int i = striped(ITEMS, j);
+                if (i < tlen) {
+                    const uint32_t r = pk.rank(j);
+                    if (r < (uint32_t)tlen) skeys[r] = k[j];
+                    else set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
+                }
+            }
+            if (VB) {
+                V v[ITEMS];
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) v[j] = svals[vs + striped(ITEMS, j)];
+                __syncthreads();
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    const uint32_t r = pk.rank(j);
+                    if (striped(ITEMS, j) < tlen && r < (uint32_t)tlen) svals[r] = v[j];
+                }
             }
         }
 
@@ -1332,11 +1358,20 @@ __device__ __forceinline__ void partition_body(const Ws &ws, const Params &p, in
         for (int r = 0; r < ITEMS; r++) {
             const int i = r * kThreads + tid;
             if (i < tlen) {
-                const Raw kk = skeys[i];
+                Raw kk;
+                V vv{};
+                if constexpr (KV8) {
+                    const uint2 e = reinterpret_cast<const uint2 *>(s.keys)[i];
+                    kk = e.x;
+                    vv = e.y;
+                } else {
+                    kk = skeys[i];
+                    if (VB) vv = svals[i];
+                }
                 const uint32_t at = (uint32_t)(s.offs[KT::bits_at(enc(kk), bk.pos, p.bits)] + i);
                 if (at < bk.len) {
                     dst[at] = kk;
-                    if (VB) vdst[at] = svals[i];
+                    if (VB) vdst[at] = vv;
                 } else {
                     set_status(ws.ctr, BINAR_ERR_DEVICE_BOUNDS);
                 }
