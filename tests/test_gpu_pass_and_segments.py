@@ -39,6 +39,25 @@ def test_partition_pass_against_oracle(kind, pos, n):
     assert np.array_equal(to_host(offs2), eoffs)
 
 
+
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("pos", [0, 24])
+@pytest.mark.parametrize("n", [6144, 12288, 18433, 61440])
+def test_partition_pass_full_tiles_with_random_payloads(n, pos, tile):
+    """4-byte keys with 4-byte payloads are staged as 8-byte records that fill
+    the tile's key and payload buffers: sizes that are whole tiles of both
+    shapes (6144 and 4096 keys: every tile full) and one key past them,
+    payloads unrelated to the keys."""
+    g = np.random.Generator(np.random.PCG64(7000 + n + pos))
+    keys = inputs.uniform_keys(n, np.uint32, g)
+    vals = inputs.uniform_keys(n, np.uint32, g)
+    cfg = {"tile_keys": binding.tile_choices(4, 4)[tile]}
+    ko, vo, offs = binding.partition_pass(to_dev(keys), to_dev(vals), pos=pos, config=cfg)
+    ek, ev, eoffs = oracle.partition_pass(keys, vals, key_map=key_map_of(keys), pos=pos, k=8)
+    assert same_bits(to_host(ko), ek)
+    assert same_bits(to_host(vo), ev)
+    assert np.array_equal(to_host(offs), eoffs)
+
 def test_partition_pass_empty():
     keys = np.zeros(0, dtype=np.uint32)
     _, _, offs = binding.partition_pass(to_dev(keys), None, pos=0)
